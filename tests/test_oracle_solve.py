@@ -1,0 +1,219 @@
+"""Pins of the oracle's forward solvers (Alg. 1 and the ordered solve).
+
+Each check uses something the paper or the mathematics fixes, not the
+oracle itself:
+* the drift example printed in the paper (golden fixture);
+* lattice-ray exactness of the closed form |x - x_s|_M + w.(x - x_s) for
+  constant coefficients, and T >= closed form everywhere;
+* the closed-form error falling with h (paper: sub-1 % relative L2);
+* T <= D8, the shortest path on the 8-neighbour graph (scipy's Dijkstra);
+* Gauss-Seidel and the ordered solve agreeing to 1e-12 with zero residual;
+* homogeneity, h-scaling, D4 symmetry and monotonicity in the sources.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.sparse import coo_matrix
+from scipy.sparse.csgraph import dijkstra
+
+import oracle as O
+import rf_inputs as R
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+DX = [-1, -1, -1, 0, 1, 1, 1, 0]
+DY = [1, 0, -1, -1, -1, 0, 1, 1]
+
+
+def solve(raw, src, h, eps=0.0, delta=0.05):
+    proj, _ = O.project(raw, eps, delta)
+    T, it, st, _ = O.solve_gs(proj, src, h, eps)
+    assert st == O.OK
+    return T, proj
+
+
+def closed_form(ny, nx, h, M, w, si, sj):
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    dx = (x - sj) * h
+    dy = (y - si) * h
+    return np.sqrt(M[0, 0] * dx * dx + 2 * M[0, 1] * dx * dy + M[1, 1] * dy * dy) + w[0] * dx + w[1] * dy
+
+
+def test_drift_example_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "drift_example.txt")) if l.strip() and l[0] != "#"]
+    n = 61
+    raw = R.constant_fields(n, n, np.eye(2), (-0.3, 0.0))
+    src = R.point_sources(n, n, [(30, 30)])
+    T, _ = solve(raw, src, 1.0)
+    wx = float(np.float32(-0.3))  # the input is rounded to float32 once
+    for off, expect in rows:
+        off, expect = int(off), float(expect)
+        got = T[30, 30 + off]
+        # expect is printed for w = -0.3 exactly; the float32 input shifts it
+        # by |off| * (wx + 0.3) * sign
+        assert got == pytest.approx(expect + off * (wx + 0.3), abs=1e-9)
+        assert got == pytest.approx(expect, rel=1e-6)
+
+
+@pytest.mark.parametrize("theta,lam,w", [(0.0, (4.0, 0.25), (0.0, 0.0)),
+                                         (math.pi / 4, (4.0, 0.25), (0.1, -0.2)),
+                                         (math.pi / 6, (2.0, 0.5), (-0.2, -0.1))])
+def test_constant_metric_lattice_rays_exact(theta, lam, w):
+    n = 41
+    h = 1.0 / (n - 1)
+    Rm = np.array([[math.cos(theta), -math.sin(theta)], [math.sin(theta), math.cos(theta)]])
+    M = Rm @ np.diag(lam) @ Rm.T
+    raw = R.constant_fields(n, n, M, w)
+    # the solver sees the float32-rounded factor: rebuild M from it
+    l11, l21, l22, wx, wy = [float(raw[c, 0, 0]) for c in range(5)]
+    Mf = np.array([[l11 * l11, l11 * l21], [l11 * l21, l21 * l21 + l22 * l22]])
+    wf = np.array([wx, wy])
+    src = R.point_sources(n, n, [(20, 20)])
+    T, _ = solve(raw, src, h)
+    Tc = closed_form(n, n, h, Mf, wf, 20, 20)
+    # never below the closed form (linear interpolation of a convex cost)
+    assert (T - Tc).min() > -1e-12
+    for k in range(8):
+        for s in range(1, 21):
+            i, j = 20 + s * DY[k], 20 + s * DX[k]
+            assert T[i, j] == pytest.approx(Tc[i, j], rel=1e-12, abs=1e-14)
+
+
+def test_error_falls_with_h():
+    # G = diag(4, 0.25) (the paper's uniform anisotropic case) and G = I
+    for lam in ((4.0, 0.25), (1.0, 1.0)):
+        M = np.diag(lam)
+        errs = []
+        for n in (26, 51, 101, 201):
+            h = 1.0 / (n - 1)
+            raw = R.constant_fields(n, n, M, (0.0, 0.0))
+            c = n // 2
+            src = R.point_sources(n, n, [(c, c)])
+            T, _ = solve(raw, src, h)
+            Tc = closed_form(n, n, h, M, (0.0, 0.0), c, c)
+            errs.append(np.linalg.norm(T - Tc) / np.linalg.norm(Tc))
+        assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
+        assert errs[-1] < 0.01, errs
+
+
+def d8_shortest_paths(proj, src, h):
+    """Shortest path on the directed 8-neighbour graph, weight of edge q->p
+    = F_p(x_p - x_q) with F_p the Randers cost of node p."""
+    _, ny, nx = proj.shape
+    l11, l21, l22, wx, wy = proj
+    m11 = l11 * l11
+    m12 = l11 * l21
+    m22 = l21 * l21 + l22 * l22
+    rows, cols, vals = [], [], []
+    for i in range(ny):
+        for j in range(nx):
+            p = i * nx + j
+            for k in range(8):
+                ii, jj = i + DY[k], j + DX[k]
+                if 0 <= ii < ny and 0 <= jj < nx:
+                    vx, vy = -h * DX[k], -h * DY[k]  # travel from q to p
+                    c = math.sqrt(m11[i, j] * vx * vx + 2 * m12[i, j] * vx * vy + m22[i, j] * vy * vy) \
+                        + wx[i, j] * vx + wy[i, j] * vy
+                    rows.append(ii * nx + jj)
+                    cols.append(p)
+                    vals.append(c)
+    G = coo_matrix((vals, (rows, cols)), shape=(ny * nx, ny * nx)).tocsr()
+    d = dijkstra(G, directed=True, indices=np.flatnonzero(src.ravel()), min_only=True)
+    return d.reshape(ny, nx)
+
+
+def test_dijkstra_bound_on_small_grid():
+    ny, nx = 19, 23
+    h = 1.0 / 22
+    raw = R.randers_fields(ny, nx, h, 8, seed=5, omega="unit", omega_scale=0.3)
+    src = R.point_sources(ny, nx, [(9, 11)])
+    T, proj = solve(raw, src, h, eps=0.0)
+    D = d8_shortest_paths(O._d(proj), src, h)
+    assert (T - D).max() < 1e-12
+    assert (D - T).max() > 1e-4  # the two-point updates do lower T
+
+
+@pytest.mark.parametrize("which", ["config1", "ragged", "config2"])
+def test_gauss_seidel_agrees_with_ordered(which):
+    if which == "config1":
+        c = R.config1()
+    elif which == "config2":
+        c = R.config2()
+    else:
+        ny, nx = 37, 53
+        h = 1.0 / 52
+        c = dict(raw=R.randers_fields(ny, nx, h, 8, seed=3, omega="field", omega_max=1.0),
+                 src=R.random_sources(ny, nx, 3, seed=3), h=h, eps=1e-6, delta=0.2)
+    proj, _ = O.project(c["raw"], c["eps"], c["delta"])
+    T1, it, st, _ = O.solve_gs(proj, c["src"], c["h"], c["eps"])
+    assert st == O.OK
+    T2, st2 = O.solve_ordered(proj, c["src"], c["h"], c["eps"])
+    assert st2 == O.OK
+    assert np.all(np.isfinite(T1))
+    assert np.abs(T1 - T2).max() <= 1e-12 * max(1.0, T1.max())
+    assert np.abs(O.residual(proj, c["src"], c["h"], c["eps"], T1)).max() == 0.0
+    assert np.abs(O.residual(proj, c["src"], c["h"], c["eps"], T2)).max() == 0.0
+
+
+def test_min_update_reading_can_stall():
+    """The literal min-update of Alg. 1 (T <- min(T, t)) stops at a state that
+    is not a fixed point on this workload (causality rejections make the
+    candidate function non-monotone); the replacement update does not.
+    This pins the reading used by both solvers."""
+    c = R.config2()
+    proj, _ = O.project(c["raw"], c["eps"], c["delta"])
+    Tm, _, st, _ = O.solve_gs(proj, c["src"], c["h"], c["eps"], replace=False)
+    res = O.residual(proj, c["src"], c["h"], c["eps"], Tm)
+    assert np.abs(res).max() > 0.0
+
+
+def test_homogeneity_and_h_scaling():
+    ny, nx = 30, 34
+    h = 1.0 / 33
+    raw = R.randers_fields(ny, nx, h, 8, seed=7, omega="unit", omega_scale=0.3).astype(np.float64)
+    src = R.random_sources(ny, nx, 2, seed=7)
+    T, _ = solve(raw, src, h, eps=0.0, delta=0.05)
+    c = 1.75
+    T2, _ = solve(raw * c, src, h, eps=0.0, delta=0.05)
+    assert np.allclose(T2, c * T, rtol=1e-12, atol=0)
+    T3, _ = solve(raw, src, 2.0 * h, eps=0.0, delta=0.05)
+    assert np.allclose(T3, 2.0 * T, rtol=1e-12, atol=0)
+
+
+def test_d4_symmetry_isotropic():
+    n = 33
+    raw = R.constant_fields(n, n, np.eye(2) * 2.0, (0.0, 0.0))
+    src = R.point_sources(n, n, [(16, 16)])
+    T, _ = solve(raw, src, 1.0 / 32)
+    for S in (T[::-1], T[:, ::-1], T.T, T[::-1, ::-1].T):
+        assert np.allclose(S, T, rtol=1e-13, atol=1e-15)
+
+
+def test_more_sources_never_raise_T():
+    ny, nx = 40, 40
+    h = 1.0 / 39
+    raw = R.randers_fields(ny, nx, h, 8, seed=11, omega="unit", omega_scale=0.2)
+    s1 = R.point_sources(ny, nx, [(10, 12)])
+    s2 = s1.copy()
+    s2[30, 25] = 1
+    T1, _ = solve(raw, s1, h)
+    T2, _ = solve(raw, s2, h)
+    assert (T2 - T1).max() <= 1e-15
+    assert (T1 - T2).max() > 0.1
+
+
+def test_no_source_is_an_error():
+    raw = R.constant_fields(8, 8, np.eye(2), (0.0, 0.0))
+    proj, _ = O.project(raw, 0.0, 0.05)
+    T, it, st, _ = O.solve_gs(proj, np.zeros((8, 8), np.uint8), 0.1, 0.0)
+    assert st == O.ERR_NO_SOURCE
+    T, st = O.solve_ordered(proj, np.zeros((8, 8), np.uint8), 0.1, 0.0)
+    assert st == O.ERR_NO_SOURCE
+
+
+def test_all_sources_is_all_zero():
+    raw = R.constant_fields(6, 7, np.eye(2), (0.1, 0.0))
+    proj, _ = O.project(raw, 0.0, 0.05)
+    T, it, st, _ = O.solve_gs(proj, np.ones((6, 7), np.uint8), 0.1, 0.0)
+    assert st == O.OK and np.all(T == 0.0)
