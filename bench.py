@@ -1,0 +1,343 @@
+"""Benchmark: forward+adjoint solves/s of the differentiable Randers eikonal
+solver on a 2048x2048 grid (the inverse-problem workload), one GB300.
+
+A step is one pass of the whole hot path over one grid: feasibility
+projection -> forward fast sweep -> stencil record -> adjoint (lambda and
+parameter gradients) -> projection backward, on seeded synthetic fields
+(16-mode Fourier metric, |w| = 0.3 drift, 4 sources, dL/dT on 0.5 % of the
+nodes).  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (a 256 MB write) between timed steps.  `e2e` repeats the step
+through the public API from pinned HOST buffers with the host<->device
+copies inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun), every rank solves its own grid (independent
+replicas; a single grid does not shard) and the value is the whole-job
+aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "forward+adjoint solves/s at 2048x2048"
+UNIT = "solves/s"
+ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-update
+LAUNCHES_PER_STEP = 7      # project, init, source check, sweep, record, adjoint, project backward
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--size", type=int, default=2048)
+    p.add_argument("--algo", default="sweep", choices=["sweep", "ordered"])
+    p.add_argument("--band", type=int, default=0)
+    p.add_argument("--block", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(n):
+    return {"workload": f"inverse-problem forward+adjoint step, {n}x{n} FP32 grid",
+            "grid": [n, n], "h": 1.0 / (n - 1), "fourier_modes": 16, "drift": "|w|_2 = 0.3 direction field",
+            "sources": 4, "observed_fraction": 0.005, "eps": 1e-6, "delta": 0.05,
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            if self._stop.is_set():
+                break
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self):
+        self._stop.set()
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(n_sample, n_full, seed=0):
+    """One forward+adjoint of the FP64 oracle (single thread) on an
+    n_sample^2 grid built by the same recipe; returns seconds scaled to one
+    n_full^2 solve (work is linear in nodes at a fixed sweep count)."""
+    import oracle as O
+    import rf_inputs as R
+    c = R.config_inverse(n=n_sample, seed=seed)
+    t0 = time.perf_counter()
+    out = O.solve_and_grad(c["raw"].astype(np.float64), c["src"], c["h"], c["eps"], c["delta"],
+                           c["g"].astype(np.float64))
+    dt = time.perf_counter() - t0
+    scale = (n_full * n_full) / float(n_sample * n_sample)
+    return dt * scale, dt, out["iters"]
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    n_sample = 512
+    for _ in range(args.warmup):
+        oracle_sample(n_sample, args.size)
+    times = []
+    for k in range(args.steps):
+        t_full, t_raw, iters = oracle_sample(n_sample, args.size, seed=k)
+        times.append(t_full)
+    per = statistics.mean(times)
+    value = 1.0 / per
+    sample = (f"FP64 oracle, one thread: one forward+adjoint per step on a {n_sample}x{n_sample} grid of the "
+              f"same recipe, time x{(args.size / n_sample) ** 2:.0f} to the {args.size}^2 solve")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.size),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_ours(args):
+    import torch
+
+    import rf_inputs as R
+    from paper_2603_00035_gb300 import api
+    from paper_2603_00035_gb300 import build as B
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n = args.size
+    c = R.config_inverse(n=n, seed=rank)
+    eps, delta, h = c["eps"], c["delta"], c["h"]
+    raw = torch.from_numpy(c["raw"]).to(dev)
+    src = torch.from_numpy(c["src"]).to(dev)
+    g = torch.from_numpy(c["g"]).to(dev)
+    ctx = api.Context.get(local)
+    opts = api.make_opts(band=args.band, block=args.block)
+    stream = torch.cuda.current_stream()
+    # preallocated outputs: the timed steps allocate nothing
+    proj = torch.empty_like(raw)
+    clip = torch.empty((n, n), dtype=torch.uint8, device=dev)
+    T = torch.empty((n, n), dtype=torch.float32, device=dev)
+    rec = api.Record.empty(n, n, dev)
+    gproj = torch.empty_like(raw)
+    lam = torch.empty((n, n), dtype=torch.float32, device=dev)
+    graw = torch.empty_like(raw)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        api.rf_project(raw, eps, delta, proj5=proj, clip=clip, ctx=ctx)
+        if events:
+            events[1].record(stream)
+        api.rf_sweep_forward(proj, eps, src, h, opts=opts, T=T, record=False, ctx=ctx)
+        if events:
+            events[2].record(stream)
+        api.rf_record_stencils(proj, eps, src, h, T, rec=rec, ctx=ctx)
+        if events:
+            events[3].record(stream)
+        api.rf_adjoint(src, T, rec, g, algo=args.algo, lam=False, dLdproj5=gproj, ctx=ctx)
+        if events:
+            events[4].record(stream)
+        api.rf_project_backward(raw, clip, eps, delta, gproj, draw5=graw, ctx=ctx)
+        if events:
+            events[5].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    st = ctx.stats()
+    if st["status"] != 0:
+        raise RuntimeError(f"solver status {st}")
+    sweeps, adj_sweeps, cell_updates = st["sweeps"], st["adj_sweeps"], st["cell_updates"]
+
+    phase = np.zeros(5)
+    total_ms = 0.0
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        step(ev)
+        torch.cuda.synchronize()
+        ph = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+        phase += np.array(ph)
+        total_ms += ev[0].elapsed_time(ev[5])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.stop()
+    st = ctx.stats()
+    if st["status"] != 0:
+        raise RuntimeError(f"solver status {st}")
+
+    # e2e: public API from pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_raw = torch.from_numpy(c["raw"]).pin_memory()
+        h_src = torch.from_numpy(c["src"]).pin_memory()
+        h_g = torch.from_numpy(c["g"]).pin_memory()
+        h_T = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        h_graw = torch.empty((5, n, n), dtype=torch.float32).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_ms = 0.0
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            raw.copy_(h_raw, non_blocking=True)
+            src.copy_(h_src, non_blocking=True)
+            g.copy_(h_g, non_blocking=True)
+            step()
+            h_T.copy_(T, non_blocking=True)
+            h_graw.copy_(graw, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                e2e_ms += e0.elapsed_time(e1)
+        h2d = h_raw.numel() * 4 + h_src.numel() + h_g.numel() * 4
+        d2h = h_T.numel() * 4 + h_graw.numel() * 4
+        e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # max over ranks of the timed region
+    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t_local.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    phase_ms = phase / args.steps
+    names = ["project", "sweep_forward", "record", "adjoint", "project_backward"]
+    dom = int(np.argmax(phase_ms))
+    peak, peak_kind = measured_peaks()
+    if names[dom] == "sweep_forward":
+        bytes_per_launch = ALG_BYTES_PER_UPDATE * cell_updates
+    elif names[dom] == "adjoint":
+        # per node per adjoint sweep: id 1 B + w1 4 B + lambda read 4 B + write 4 B + g 4 B + T 4 B
+        bytes_per_launch = 21 * adj_sweeps * n * n + 44 * n * n
+    else:
+        bytes_per_launch = 60 * n * n
+    achieved = bytes_per_launch / (phase_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(n),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "clocks": sampler.summary(),
+            "solver": {"sweeps": sweeps, "adj_sweeps": adj_sweeps, "cell_updates": cell_updates,
+                       "gcell_updates_per_s": cell_updates / (phase_ms[1] / 1e3) / 1e9,
+                       "phase_ms": dict(zip(names, [round(float(x), 4) for x in phase_ms])),
+                       "algo": args.algo}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_full, t_raw, iters = oracle_sample(1024, n)
+        line["cpu_baseline"] = {"value": 1.0 / t_full, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 oracle, one thread: one forward+adjoint on a 1024x1024 grid of the "
+                                          f"same recipe ({t_raw:.2f} s, {iters} iterations), time x4 to the "
+                                          f"{n}^2 solve"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

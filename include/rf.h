@@ -1,0 +1,193 @@
+/*
+ * rf.h -- C ABI of librf, the GB300 (sm_103a) implementation of the hot path
+ * of "Differentiable Randers-Finsler Eikonal Solvers" (arXiv 2603.00035):
+ * feasibility projection, fast-sweep forward solve with stencil record, and
+ * the adjoint of the converged discrete system.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grids are row-major [ny][nx] float32; node (i,j) sits at (x,y) =
+ *    (j h, i h).  Neighbour n of a node is at offset (dx,dy) with
+ *    n = 0..7 -> (-1,+1) (-1,0) (-1,-1) (0,-1) (+1,-1) (+1,0) (+1,+1) (0,+1)
+ *    (counter-clockwise from the upper-left, Fig. 4a); stencil k pairs
+ *    neighbours k and (k+1) mod 8.
+ *  - A "5-plane" array is 5 consecutive planes of ny*nx float32 values:
+ *    L11, L21, L22, wx, wy (the metric factor and the drift).  The metric is
+ *    M = L L^T + eps I, L lower-triangular; the Randers cost of a
+ *    displacement v is F(v) = sqrt(v^T M v) + w^T v.  In the paper's
+ *    notation (Eq. 1-3) this is G = M and b = -w.
+ *  - Every pointer argument is DEVICE memory owned by the caller unless the
+ *    comment says otherwise; the library never frees it.  All work is
+ *    enqueued on `stream` (a cudaStream_t passed as void*; NULL = the legacy
+ *    default stream) and is asynchronous unless stated.
+ *  - Every call returns rf_status.  Host-detectable problems (null pointers,
+ *    bad sizes) return immediately without enqueuing work.  Problems found on
+ *    the device are written to the context's device status word and are
+ *    returned by rf_ctx_last_stats() after the stream is synchronised.
+ *  - One rf_ctx serves one stream at a time (its workspace is shared).
+ */
+#ifndef RF_H_
+#define RF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rf_status {
+  RF_OK = 0,
+  RF_ERR_INVALID_ARG = 1,     /* null pointer, size < 1, h <= 0, ...        */
+  RF_ERR_CUDA = 2,            /* a CUDA runtime call failed                 */
+  RF_ERR_NOT_CONVERGED = 3,   /* max_sweeps reached; T/lambda still written */
+  RF_ERR_TIMEOUT = 4,         /* a bounded device wait expired              */
+  RF_ERR_NONFINITE_INPUT = 5, /* NaN/Inf in an input field                  */
+  RF_ERR_NO_SOURCE = 6,       /* the source mask is empty                   */
+  RF_ERR_NO_MEMORY = 7,       /* workspace allocation failed                */
+  RF_ERR_UNSUPPORTED = 8      /* configuration not supported on this device */
+} rf_status;
+
+typedef struct rf_ctx rf_ctx;
+
+typedef struct rf_grid {
+  int32_t ny, nx; /* rows (y) and columns (x); each >= 1                   */
+  float h;        /* grid spacing, > 0                                      */
+} rf_grid;
+
+enum rf_mode {
+  RF_MODE_COLD = 0, /* T = 0 on sources, +inf elsewhere, then sweep          */
+  RF_MODE_WARM = 1  /* start from the caller's T (sources forced to 0)       */
+};
+
+enum rf_adjoint_algo {
+  RF_ADJ_SWEEP = 0, /* transposed line sweeps until lambda stops changing   */
+  RF_ADJ_ORDERED = 1 /* radix sort on T, then dependency-ordered gather     */
+};
+
+typedef struct rf_opts {
+  float tol;          /* a node counts as changed when |T_new - T_old| > tol;
+                         0 = exact (stop at the first sweep that changes
+                         nothing, which is then a fixed point)              */
+  int32_t max_sweeps; /* cap on directional sweeps (4 per iteration)       */
+  int32_t mode;       /* enum rf_mode                                       */
+  int32_t band;       /* lines per band (0 = auto)                          */
+  int32_t block;      /* line steps per block, <= band (0 = auto)           */
+} rf_opts;
+
+/* Per-node record of the converged forward solve (Alg. 2, first loop). */
+typedef struct rf_record {
+  uint8_t *id; /* [ny*nx] 0 = source/unreached; 0x10|n = one-point through
+                  neighbour n; 0x20|k = two-point on stencil k            */
+  float *w1;   /* [ny*nx] dT0/dT(first donor) (1 for one-point); the second
+                  donor's weight is 1 - w1                                */
+  float *dT;   /* [5*ny*nx] dT0/d(L11, L21, L22, wx, wy), 5 planes        */
+} rf_record;
+
+typedef struct rf_stats {
+  int32_t status;       /* rf_status found on the device                  */
+  int32_t sweeps;       /* directional sweeps run (forward) / adjoint     */
+  int32_t converged;    /* 1 if the last sweep changed nothing            */
+  int32_t adj_sweeps;   /* sweeps of the last adjoint (RF_ADJ_SWEEP)      */
+  int64_t cell_updates; /* sweeps * ny * nx of the last forward           */
+  float max_residual;   /* max |T - min valid candidate(T)| (record pass) */
+  float pad;
+} rf_stats;
+
+/* ---- context ------------------------------------------------------------
+ * rf_ctx_create: binds a context to CUDA device `device`, allocates a small
+ * fixed workspace.  Larger buffers (the second sweep buffer, adjoint
+ * buffers) are allocated on first use and grown on demand; a call that must
+ * grow them allocates with cudaMalloc, so call once at full size before
+ * capturing a CUDA graph.  rf_ctx_destroy frees everything the context owns
+ * (not caller buffers). */
+rf_status rf_ctx_create(rf_ctx **ctx, int device);
+rf_status rf_ctx_destroy(rf_ctx *ctx);
+
+/* Bound (nanoseconds, >= 0) on every device-side wait of the kernels this
+ * context launches (neighbour progress flags, grid barriers).  When a wait
+ * expires the kernel records RF_ERR_TIMEOUT, every CTA leaves its loops and
+ * the launch ends; the context stays usable.  Default 2e9 (2 s). */
+rf_status rf_ctx_set_timeout(rf_ctx *ctx, int64_t timeout_ns);
+
+/* Synchronise the stream of the context's last call and copy the device
+ * statistics (including the device status word) into *out (host memory).
+ * Returns out->status. */
+rf_status rf_ctx_last_stats(rf_ctx *ctx, rf_stats *out);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *rf_status_string(rf_status s);
+
+/* ---- a1: feasibility projection -----------------------------------------
+ * Paper: App. B "Feasibility Projections" (the G^-1-norm of b) and the
+ * spec form M = L L^T + eps I.  For each node:
+ *   n = |w|_{M^-1} = sqrt((wx^2 M22 - 2 wx wy M12 + wy^2 M11) / det M),
+ *   w_out = w * min(1, (1 - delta) / n);
+ * L passes through.  raw5, proj5: 5-plane arrays (may alias only if equal);
+ * clip: [ny*nx] uint8, 1 where the drift was rescaled (n > 1 - delta).
+ * eps >= 0, 0 < delta < 1.  A NaN/Inf input sets RF_ERR_NONFINITE_INPUT in
+ * the device status word. */
+rf_status rf_project(rf_ctx *ctx, const rf_grid *grid, const float *raw5,
+                     float eps, float delta, float *proj5, uint8_t *clip,
+                     void *stream);
+
+/* a9: backward of rf_project.  dproj5 = dL/d(L11, L21, L22, w_out x, w_out
+ * y) (5 planes); draw5 = dL/d(raw inputs) (5 planes, may alias dproj5).  For
+ * a clipped node, with P = M^-1, g = dL/dw_out, c = 1 - delta:
+ *   dL/dw = (c/n)(g - P w (w^T g)/n^2),
+ *   dL/dM += c (w^T g)/(2 n^3) (P w)(P w)^T,  dL/dL = 2 (dL/dM) L. */
+rf_status rf_project_backward(rf_ctx *ctx, const rf_grid *grid,
+                              const float *raw5, const uint8_t *clip,
+                              float eps, float delta, const float *dproj5,
+                              float *draw5, void *stream);
+
+/* ---- a2-a5: forward solve -------------------------------------------------
+ * Paper: Sec. 3.2 (Eqs. 2-3), App. A "Forward Solve Pseudocode" (Alg. 1).
+ * proj5: projected 5-plane fields; src: [ny*nx] uint8 source mask (non-zero
+ * = source, T = 0).  T: [ny*nx] output (and input guess when opts->mode ==
+ * RF_MODE_WARM).  Each node takes the minimum over its valid one-point and
+ * two-point candidates; sweeps run in the order columns +x, rows +y,
+ * columns -x, rows -y, every line of a sweep updated as a parallel front,
+ * until a sweep changes nothing (or opts->max_sweeps).  Convergence is
+ * decided on the device.  Unreached nodes stay +inf.
+ * rec (nullable): when given, the stencil id, donor weight and the partials
+ * dT0/dtheta of every node's winning update at the converged T are written
+ * (Alg. 2 "Identify active stencil"; App. A closed-form partials), plus the
+ * max residual into the stats.  opts may be NULL (defaults: tol 0,
+ * max_sweeps 64, cold start, automatic band/block). */
+rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid,
+                           const float *proj5, float eps, const uint8_t *src,
+                           const rf_opts *opts, float *T, rf_record *rec,
+                           void *stream);
+
+/* a5 alone: stencil identification and closed-form partials of a given
+ * (converged) T -- the record rf_sweep_forward writes when rec != NULL.
+ * Paper: Alg. 2 "Identify active stencil"; App. A closed-form partials.
+ * Also stores max |T - min valid candidate(T)| in the context statistics. */
+rf_status rf_record_stencils(rf_ctx *ctx, const rf_grid *grid,
+                             const float *proj5, float eps, const uint8_t *src,
+                             const float *T, rf_record *rec, void *stream);
+
+/* B7: residual r = T - min valid candidate(T) at every non-source node.
+ * res (nullable): [ny*nx] per-node residual; max_abs (device float*,
+ * nullable): max |r| over nodes with finite T. */
+rf_status rf_residual(rf_ctx *ctx, const rf_grid *grid, const float *proj5,
+                      float eps, const uint8_t *src, const float *T,
+                      float *res, float *max_abs, void *stream);
+
+/* ---- a6-a8: adjoint ---------------------------------------------------------
+ * Paper: Sec. 3.3 (Eqs. 4-6), App. A Alg. 2 and the closed-form partials.
+ * Solves lambda_p = g_p + sum over children q (neighbours whose recorded
+ * update uses p as a donor) of dT_q/dT_p lambda_q -- the unit-diagonal form
+ * of J^T lambda = g -- then writes dL/dtheta_p = lambda_p dT0_p/dtheta_p
+ * into dLdproj5 (5 planes, zero at sources and unreached nodes).
+ * T, rec: from rf_sweep_forward; dLdT: [ny*nx] (ignored where T = +inf);
+ * lambda (nullable): [ny*nx] output.  algo: enum rf_adjoint_algo. */
+rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src,
+                     const float *T, const rf_record *rec, const float *dLdT,
+                     float *dLdproj5, float *lambda, int algo, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RF_H_ */

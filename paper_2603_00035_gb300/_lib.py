@@ -1,0 +1,94 @@
+"""ctypes binding of librf (include/rf.h).  Marshalling only: every step of
+the solver runs in the CUDA library; if librf.so cannot be loaded this
+module raises -- there is no fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "rf.h")
+LIB_PATH = os.path.join(HERE, "librf.so")
+
+STATUS = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_CUDA", 3: "RF_ERR_NOT_CONVERGED",
+          4: "RF_ERR_TIMEOUT", 5: "RF_ERR_NONFINITE_INPUT", 6: "RF_ERR_NO_SOURCE",
+          7: "RF_ERR_NO_MEMORY", 8: "RF_ERR_UNSUPPORTED"}
+RF_OK, RF_ERR_INVALID_ARG, RF_ERR_CUDA, RF_ERR_NOT_CONVERGED, RF_ERR_TIMEOUT = 0, 1, 2, 3, 4
+RF_ERR_NONFINITE_INPUT, RF_ERR_NO_SOURCE, RF_ERR_NO_MEMORY, RF_ERR_UNSUPPORTED = 5, 6, 7, 8
+RF_MODE_COLD, RF_MODE_WARM = 0, 1
+RF_ADJ_SWEEP, RF_ADJ_ORDERED = 0, 1
+
+
+class RFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("h", ctypes.c_float)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_float), ("max_sweeps", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("band", ctypes.c_int32), ("block", ctypes.c_int32)]
+
+
+class Record(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_void_p), ("w1", ctypes.c_void_p), ("dT", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("adj_sweeps", ctypes.c_int32), ("cell_updates", ctypes.c_int64),
+                ("max_residual", ctypes.c_float), ("pad", ctypes.c_float)]
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions include/rf.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rf_[a-z_0-9]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load librf.so (built by paper_2603_00035_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librf.so not found at {path}: run paper_2603_00035_gb300.build.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    sig = {
+        "rf_ctx_create": [ctypes.POINTER(P), I],
+        "rf_ctx_destroy": [P],
+        "rf_ctx_set_timeout": [P, ctypes.c_int64],
+        "rf_ctx_last_stats": [P, ctypes.POINTER(Stats)],
+        "rf_project": [P, ctypes.POINTER(Grid), P, F, F, P, P, P],
+        "rf_project_backward": [P, ctypes.POINTER(Grid), P, P, F, F, P, P, P],
+        "rf_sweep_forward": [P, ctypes.POINTER(Grid), P, F, P, ctypes.POINTER(Opts), P,
+                             ctypes.POINTER(Record), P],
+        "rf_residual": [P, ctypes.POINTER(Grid), P, F, P, P, P, P, P],
+        "rf_record_stencils": [P, ctypes.POINTER(Grid), P, F, P, P, ctypes.POINTER(Record), P],
+        "rf_adjoint": [P, ctypes.POINTER(Grid), P, P, ctypes.POINTER(Record), P, P, P, I, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.rf_status_string.argtypes = [I]
+    lib.rf_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status: int, where: str):
+    if status != RF_OK:
+        raise RFError(status, where)

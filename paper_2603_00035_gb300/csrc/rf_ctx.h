@@ -1,0 +1,64 @@
+// rf_ctx.h -- internal definition of rf_ctx (the library's workspace) and
+// helpers shared by the entry points.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rf.h"
+#include "rf_device.cuh"
+
+struct rf_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t last_stream = nullptr;
+  rf::DevState *state = nullptr;  // device status word and counters
+  long long timeout_ns = 2000000000LL;  // bound of every device wait
+
+  // grown on demand
+  unsigned *progress = nullptr;  // per-band progress tokens
+  size_t progress_cap = 0;
+  int *changed = nullptr;  // per-sweep changed flags
+  size_t changed_cap = 0;
+  float *tbuf = nullptr;  // second buffer of the ping-pong sweeps
+  size_t tbuf_cap = 0;
+  float *lbuf = nullptr;  // adjoint: lambda ping-pong buffers
+  size_t lbuf_cap = 0;
+  void *scratch = nullptr;  // adjoint (ordered): sort keys/values/temp
+  size_t scratch_cap = 0;
+};
+
+namespace rf {
+
+inline rf_status cuda_status(cudaError_t e) {
+  return e == cudaSuccess ? RF_OK : RF_ERR_CUDA;
+}
+
+template <class T>
+inline rf_status ensure(T **ptr, size_t *cap, size_t count) {
+  if (*cap >= count && *ptr) return RF_OK;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  size_t n = count < 1 ? 1 : count;
+  if (cudaMalloc((void **)ptr, n * sizeof(T)) != cudaSuccess) {
+    *ptr = nullptr;
+    return RF_ERR_NO_MEMORY;
+  }
+  *cap = n;
+  return RF_OK;
+}
+
+inline bool grid_ok(const rf_grid *g) {
+  return g && g->ny >= 1 && g->nx >= 1 && g->h > 0.0f &&
+         (long long)g->ny * (long long)g->nx < (1LL << 31);
+}
+
+inline int blocks_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+}  // namespace rf

@@ -1,0 +1,529 @@
+// rf_sweep.cu -- a2-a5: forward fast sweep, on-device convergence, stencil
+// record and residual.
+//
+// Paper: Sec. 3.2 and App. A (Alg. 1).  One iteration is four directional
+// sweeps (columns +x, rows +y, columns -x, rows -y).  Within a sweep every
+// line (column or row) is one parallel front: node (s, l) of line step s is
+// updated from step s-1 (already updated in this sweep) and from steps s,
+// s+1 as they were before the sweep -- the column/row-parallel schedule of
+// Sec. 3.2.  The update is the replacement T <- min valid candidate
+// (equivalently Alg. 1's min-update whenever the candidate set is monotone),
+// so the sweep stops at a fixed point of T = min valid candidate(T).
+//
+// GB300 mapping.  One persistent cooperative launch runs every sweep of the
+// solve.  A sweep's lines are split into bands of R lines, one CTA per band.
+// A CTA advances its band K line steps at a time ("block"), recomputing a
+// halo of K lines on each side from the values its neighbours published at
+// the end of their previous block, so inner lines follow the exact
+// line-parallel recurrence and neighbouring CTAs synchronise once per K
+// steps instead of once per step.  T ping-pongs between two buffers so the
+// "before the sweep" values are never overwritten mid-sweep.  A tile of
+// (K+2) x (R+2K+2) times plus the K x (R+2K) metric fields of the block is
+// staged in shared memory with coalesced loads (steps are contiguous in
+// memory for column sweeps, lines for row sweeps).  Convergence: a CTA ORs
+// "some inner node changed" into a per-sweep word; after a bounded grid
+// barrier every CTA reads it and stops at the first sweep that changed
+// nothing.  Every wait is bounded by the context's timeout.
+#include <algorithm>
+
+#include "rf_ctx.h"
+#include "rf_sweep_common.cuh"
+
+namespace rf {
+
+struct SweepArgs {
+  int ny, nx;
+  float h, eps;
+  const float *f;  // 5 planes (projected)
+  const uint8_t *src;
+  float *Ta;  // caller's T (initial state, final result)
+  float *Tb;  // workspace
+  int R, K;
+  int max_sweeps;
+  float tol;
+  unsigned tok_stride;  // progress tokens per sweep
+  unsigned *progress;   // [gridDim.x]
+  int *changed;         // [max_sweeps]
+  LaunchCtl ctl;
+};
+
+// Tile geometry of one CTA (all in elements).
+struct Tile {
+  int R, K, ext, W, P, EP;
+  __device__ Tile(int R_, int K_) : R(R_), K(K_) {
+    ext = R + 2 * K;
+    W = ext + 2;
+    P = W | 1;  // odd pitch: conflict-free column-major fills
+    EP = ext | 1;
+  }
+};
+
+__host__ __device__ inline size_t sweep_smem_bytes(int R, int K) {
+  const int ext = R + 2 * K, W = ext + 2, P = W | 1, EP = ext | 1;
+  size_t fl = (size_t)(K + 2) * P + (size_t)(K + 1) * P + 5 * (size_t)K * EP;
+  return fl * sizeof(float) + (size_t)K * EP;
+}
+
+__global__ void __launch_bounds__(1024) sweep_kernel(SweepArgs a) {
+  extern __shared__ float smem[];
+  const Tile tg(a.R, a.K);
+  const int R = tg.R, K = tg.K, ext = tg.ext, W = tg.W, P = tg.P, EP = tg.EP;
+  float *old = smem;                      // (K+2) x P
+  float *nw = old + (size_t)(K + 2) * P;  // (K+1) x P
+  float *fl = nw + (size_t)(K + 1) * P;   // 5 x K x EP
+  uint8_t *sm = (uint8_t *)(fl + (size_t)5 * K * EP);  // K x EP
+  __shared__ int s_ok;
+  __shared__ int s_any;
+
+  const int tid = threadIdx.x, nth = blockDim.x, b = blockIdx.x;
+  const long long plane = (long long)a.ny * a.nx;
+  float *cur = a.Ta, *nxt = a.Tb;
+  int sweep = 0;
+  int converged = 0;
+  bool abort = false;
+
+  while (true) {
+    const int dir = sweep & 3;
+    const bool col = (dir & 1) == 0;
+    const int S = col ? a.nx : a.ny;
+    const int L = col ? a.ny : a.nx;
+    const int nb = (L + R - 1) / R;
+    const int nblk = (S + K - 1) / K;
+    const unsigned base = (unsigned)sweep * a.tok_stride;
+    int local_changed = 0;
+
+    if (b < nb && !abort) {
+      const int l0 = b * R;
+      const int line0 = l0 - K - 1;  // global line of tile column 0
+      for (int kb = 0; kb < nblk; ++kb) {
+        const int s0 = kb * K;
+        // 1. neighbours must have published block kb-1 of this sweep
+        if (tid == 0) {
+          int ok = 1;
+          if (kb > 0) {
+            if (b > 0) ok &= wait_geq(&a.progress[b - 1], base + kb, a.ctl);
+            if (ok && b + 1 < nb) ok &= wait_geq(&a.progress[b + 1], base + kb, a.ctl);
+          }
+          s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) {
+          abort = true;
+          break;
+        }
+        // 2. stage the tile: T before the sweep for steps s0-1..s0+K ...
+        const int rows_old = K + 2;
+        for (int f = tid; f < rows_old * W; f += nth) {
+          int ts, tl;
+          if (col) { tl = f / rows_old; ts = f - tl * rows_old; }
+          else     { ts = f / W;        tl = f - ts * W; }
+          const int s = s0 - 1 + ts, l = line0 + tl;
+          float v = kInf;
+          if (s >= 0 && s < S && l >= 0 && l < L) v = __ldcg(cur + gidx(dir, s, l, a.ny, a.nx));
+          old[ts * P + tl] = v;
+        }
+        // ... this sweep's values of step s0-1 (published by the neighbours)
+        for (int tl = tid; tl < W; tl += nth) {
+          const int s = s0 - 1, l = line0 + tl;
+          float v = kInf;
+          if (s >= 0 && l >= 0 && l < L) {
+            const bool halo_ok = (tl >= 1 && tl <= ext);
+            v = halo_ok ? __ldcg(nxt + gidx(dir, s, l, a.ny, a.nx))
+                        : __ldcg(cur + gidx(dir, s, l, a.ny, a.nx));
+          }
+          nw[tl] = v;
+        }
+        // ... and the fields + source flags of the K x ext computed nodes
+        for (int f = tid; f < K * ext; f += nth) {
+          int t, e;
+          if (col) { e = f / K; t = f - e * K; }
+          else     { t = f / ext; e = f - t * ext; }
+          const int s = s0 + t, l = l0 - K + e;
+          if (s < S && l >= 0 && l < L) {
+            const long long g = gidx(dir, s, l, a.ny, a.nx);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) fl[(size_t)c * K * EP + t * EP + e] = __ldg(a.f + c * plane + g);
+            sm[t * EP + e] = a.src[g];
+          }
+        }
+        __syncthreads();
+        // edge columns of the new tile (never computed): reuse old values
+        for (int t = tid; t < K; t += nth) {
+          nw[(t + 1) * P] = old[(t + 1) * P];
+          nw[(t + 1) * P + W - 1] = old[(t + 1) * P + W - 1];
+        }
+        // 3. K line steps, one parallel front each
+        for (int t = 0; t < K; ++t) {
+          const int s = s0 + t;
+          if (s >= S) break;
+          if (tid < ext) {
+            const int e = tid, tl = e + 1, l = l0 - K + e;
+            float tnew = kInf;
+            if (l >= 0 && l < L) {
+              const float told = old[(t + 1) * P + tl];
+              if (sm[t * EP + e]) {
+                tnew = 0.0f;
+              } else {
+                float Tn[8];
+#pragma unroll
+                for (int n = 0; n < 8; ++n) {
+                  int ds, dl;
+                  nb_tile_offset(dir, n, ds, dl);
+                  Tn[n] = (ds < 0) ? nw[t * P + tl + dl] : old[(t + 1 + ds) * P + tl + dl];
+                }
+                const float *fc = fl + t * EP + e;
+                const size_t cs = (size_t)K * EP;
+                const NodeConst nc = node_const(fc[0], fc[cs], fc[2 * cs], fc[3 * cs], fc[4 * cs], a.h, a.eps);
+                tnew = best_candidate(nc, Tn);
+              }
+              if (e >= K && e < K + R) {
+                const bool ch = (a.tol > 0.0f)
+                                    ? ((tnew < kInf) != (told < kInf)) || fabsf(tnew - told) > a.tol
+                                    : (__float_as_uint(tnew) != __float_as_uint(told));
+                local_changed |= ch;
+              }
+            }
+            nw[(t + 1) * P + tl] = tnew;
+          }
+          __syncthreads();
+        }
+        // 4. publish the inner lines of this block
+        for (int f = tid; f < K * R; f += nth) {
+          int t, e;
+          if (col) { e = f / K; t = f - e * K; }
+          else     { t = f / R; e = f - t * R; }
+          const int s = s0 + t, l = l0 + e;
+          if (s < S && l < L) nxt[gidx(dir, s, l, a.ny, a.nx)] = nw[(t + 1) * P + K + 1 + e];
+        }
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          st_release_u32(&a.progress[b], base + kb + 1);
+        }
+      }
+    }
+    // end of sweep: combine the changed flags, then a bounded grid barrier
+    local_changed = __syncthreads_or(local_changed);
+    if (tid == 0 && local_changed) atomicOr(&a.changed[sweep], 1);
+    if (!grid_sync(a.ctl)) abort = true;
+    if (tid == 0) s_any = ld_acquire_s32(&a.changed[sweep]);
+    __syncthreads();
+    const int any = s_any;
+    ++sweep;
+    float *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    if (abort) break;
+    if (!any) {
+      converged = 1;
+      break;
+    }
+    if (sweep >= a.max_sweeps) break;
+  }
+  // the latest values are in `cur`; hand them back in the caller's buffer
+  if (cur != a.Ta) {
+    for (long long p = (long long)blockIdx.x * nth + tid; p < plane; p += (long long)gridDim.x * nth)
+      a.Ta[p] = __ldcg(cur + p);
+  }
+  if (b == 0 && tid == 0) {
+    a.ctl.st->sweeps = sweep;
+    a.ctl.st->converged = converged;
+    a.ctl.st->cell_updates = (unsigned long long)sweep * (unsigned long long)plane;
+    if (!converged && !abort) set_error(a.ctl.st, RF_ERR_NOT_CONVERGED);
+  }
+}
+
+// Initial state: T = 0 on sources; +inf elsewhere (cold) or the guess
+// (warm).  Also flags an empty source mask.
+__global__ void init_kernel(float *T, const uint8_t *src, long long n, int warm,
+                            DevState *st, int *has_src) {
+  int any = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const bool s = src[p] != 0;
+    any |= s;
+    if (s) T[p] = 0.0f;
+    else if (!warm) T[p] = kInf;
+  }
+  if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(has_src, 1);
+}
+
+__global__ void check_source_kernel(const int *has_src, DevState *st) {
+  if (threadIdx.x == 0 && *has_src == 0) set_error(st, RF_ERR_NO_SOURCE);
+}
+
+struct RecordArgs {
+  int ny, nx;
+  float h, eps;
+  const float *f;
+  const uint8_t *src;
+  const float *T;
+  uint8_t *id;
+  float *w1;
+  float *dT;
+  float *res;  // nullable: per-node residual
+  float *max_abs;  // nullable: device float
+  DevState *st;
+};
+
+// a5: stencil identification + closed-form partials at the converged T
+// (Alg. 2 first loop; App. A partials).  For the winning update with
+// barycentric weights (w1, 1 - w1) the characteristic displacement is
+// v = w1 m1 + (1-w1) m2 (v = m_n for a one-point update) and
+//   dT0/dw = -v,   dT0/dM = v v^T / (2 |v|_M),   dT0/dL = 2 (dT0/dM) L.
+template <bool RECORD>
+__global__ void __launch_bounds__(256) record_kernel(RecordArgs a) {
+  const long long n = (long long)a.ny * a.nx;
+  float local_max = 0.0f;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p / a.nx), j = (int)(p - (long long)i * a.nx);
+    const float T0 = a.T[p];
+    uint8_t id = 0;
+    float w1 = 0.0f, d[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float r = 0.0f;
+    if (!a.src[p] && T0 < kInf) {
+      float Tn[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int ii = i + nb_dy(q), jj = j + nb_dx(q);
+        Tn[q] = (ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx) ? a.T[(long long)ii * a.nx + jj] : kInf;
+      }
+      const float l11 = a.f[p], l21 = a.f[n + p], l22 = a.f[2 * n + p], wx = a.f[3 * n + p],
+                  wy = a.f[4 * n + p];
+      const NodeConst nc = node_const(l11, l21, l22, wx, wy, a.h, a.eps);
+      const Winner w = winner(nc, Tn);
+      if (w.value < kInf) r = T0 - w.value;
+      if (RECORD && w.id) {
+        id = w.id;
+        float vx, vy;
+        const int k = w.id & 7;
+        if (w.id & 0x20) {
+          const float sum = w.l1 + w.l2;
+          w1 = sum > 0.0f ? w.l1 / sum : 0.5f;
+          const int k2 = (k + 1) & 7;
+          vx = a.h * (w1 * (float)nb_dx(k) + (1.0f - w1) * (float)nb_dx(k2));
+          vy = a.h * (w1 * (float)nb_dy(k) + (1.0f - w1) * (float)nb_dy(k2));
+        } else {
+          w1 = 1.0f;
+          vx = a.h * (float)nb_dx(k);
+          vy = a.h * (float)nb_dy(k);
+        }
+        const float m11 = fmaf(l11, l11, a.eps), m12 = l11 * l21,
+                    m22 = fmaf(l21, l21, fmaf(l22, l22, a.eps));
+        const float vm = sqrtf(vx * (m11 * vx + m12 * vy) + vy * (m12 * vx + m22 * vy));
+        const float s = 0.5f / vm;
+        const float D11 = s * vx * vx, D12 = s * vx * vy, D22 = s * vy * vy;
+        d[0] = 2.0f * (D11 * l11 + D12 * l21);
+        d[1] = 2.0f * (D12 * l11 + D22 * l21);
+        d[2] = 2.0f * D22 * l22;
+        d[3] = -vx;
+        d[4] = -vy;
+      }
+    }
+    if (RECORD) {
+      a.id[p] = id;
+      a.w1[p] = w1;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) a.dT[c * n + p] = d[c];
+    }
+    if (a.res) a.res[p] = r;
+    local_max = fmaxf(local_max, fabsf(r));
+  }
+  // block max -> one atomic per block (non-negative floats order as uints)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+  __shared__ float wmax[8];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = local_max;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(&a.st->max_res_bits, __float_as_uint(m));
+    if (a.max_abs) atomicMax((unsigned *)a.max_abs, __float_as_uint(m));
+  }
+}
+
+}  // namespace rf
+
+using namespace rf;
+
+namespace {
+
+struct SweepPlan {
+  int R, K, grid, threads;
+  size_t smem;
+};
+
+rf_status plan_sweep(rf_ctx *ctx, int ny, int nx, const rf_opts *o, SweepPlan *pl) {
+  int K = (o && o->block > 0) ? o->block : 32;
+  int R = (o && o->band > 0) ? o->band : 64;
+  if (K > R) K = R;
+  const int maxL = std::max(ny, nx);
+  int dev_max_smem = 0;
+  cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const int ext = R + 2 * K;
+    const int threads = ((ext + 31) / 32) * 32;
+    const size_t smem = sweep_smem_bytes(R, K);
+    if (threads > 1024 || (long long)smem > dev_max_smem) {
+      // shrink the block length first, then give up
+      if (K > 8) { K /= 2; continue; }
+      return RF_ERR_UNSUPPORTED;
+    }
+    cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, threads, smem) != cudaSuccess)
+      return RF_ERR_CUDA;
+    const int grid = (maxL + R - 1) / R;
+    if (per_sm > 0 && grid <= per_sm * ctx->num_sms) {
+      pl->R = R;
+      pl->K = K;
+      pl->grid = grid;
+      pl->threads = threads;
+      pl->smem = smem;
+      return RF_OK;
+    }
+    R *= 2;  // too many bands to be co-resident: widen them
+  }
+  return RF_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const float *proj5,
+                                      float eps, const uint8_t *src, const rf_opts *opts,
+                                      float *T, rf_record *rec, void *stream) {
+  if (!ctx || !grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
+  if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
+  if (rec && (!rec->id || !rec->w1 || !rec->dT)) return RF_ERR_INVALID_ARG;
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0};
+  if (opts) o = *opts;
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+    return RF_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ny = grid->ny, nx = grid->nx;
+  const long long n = (long long)ny * nx;
+
+  SweepPlan pl;
+  rf_status rs = plan_sweep(ctx, ny, nx, &o, &pl);
+  if (rs != RF_OK) return rs;
+  if ((rs = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)n)) != RF_OK) return rs;
+  if ((rs = ensure(&ctx->progress, &ctx->progress_cap, (size_t)pl.grid + 1)) != RF_OK) return rs;
+  // changed flags: [0, max_sweeps) per sweep, then has-source, then abort
+  if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2)) != RF_OK) return rs;
+
+  // reset the counters this launch uses (status word excluded: it
+  // accumulates until rf_ctx_last_stats reads it)
+  cudaMemsetAsync(ctx->progress, 0, sizeof(unsigned) * (pl.grid + 1), s);
+  cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
+  cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
+  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 3, s);
+  cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
+
+  int *has_src = ctx->changed + o.max_sweeps;  // last slot
+  init_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, src, n, o.mode == RF_MODE_WARM,
+                                                                     ctx->state, has_src);
+  check_source_kernel<<<1, 32, 0, s>>>(has_src, ctx->state);
+
+  SweepArgs a;
+  a.ny = ny;
+  a.nx = nx;
+  a.h = grid->h;
+  a.eps = eps;
+  a.f = proj5;
+  a.src = src;
+  a.Ta = T;
+  a.Tb = ctx->tbuf;
+  a.R = pl.R;
+  a.K = pl.K;
+  a.max_sweeps = o.max_sweeps;
+  a.tol = o.tol;
+  a.tok_stride = (unsigned)((std::max(ny, nx) + pl.K - 1) / pl.K + 1);
+  a.progress = ctx->progress;
+  a.changed = ctx->changed;
+  a.ctl.st = ctx->state;
+  a.ctl.abort = ctx->changed + o.max_sweeps + 1;
+  a.ctl.timeout_ns = ctx->timeout_ns;
+  void *args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)sweep_kernel, dim3(pl.grid), dim3(pl.threads),
+                                              args, pl.smem, s);
+  if (e != cudaSuccess) return RF_ERR_CUDA;
+
+  if (rec) {
+    RecordArgs r;
+    r.ny = ny;
+    r.nx = nx;
+    r.h = grid->h;
+    r.eps = eps;
+    r.f = proj5;
+    r.src = src;
+    r.T = T;
+    r.id = rec->id;
+    r.w1 = rec->w1;
+    r.dT = rec->dT;
+    r.res = nullptr;
+    r.max_abs = nullptr;
+    r.st = ctx->state;
+    cudaMemsetAsync(&ctx->state->max_res_bits, 0, sizeof(unsigned), s);
+    record_kernel<true><<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(r);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+extern "C" rf_status rf_record_stencils(rf_ctx *ctx, const rf_grid *grid, const float *proj5, float eps,
+                                        const uint8_t *src, const float *T, rf_record *rec, void *stream) {
+  if (!ctx || !grid_ok(grid) || !proj5 || !src || !T || !rec || !rec->id || !rec->w1 || !rec->dT)
+    return RF_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const long long n = (long long)grid->ny * grid->nx;
+  RecordArgs r;
+  r.ny = grid->ny;
+  r.nx = grid->nx;
+  r.h = grid->h;
+  r.eps = eps;
+  r.f = proj5;
+  r.src = src;
+  r.T = T;
+  r.id = rec->id;
+  r.w1 = rec->w1;
+  r.dT = rec->dT;
+  r.res = nullptr;
+  r.max_abs = nullptr;
+  r.st = ctx->state;
+  cudaMemsetAsync(&ctx->state->max_res_bits, 0, sizeof(unsigned), s);
+  record_kernel<true><<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(r);
+  return cuda_status(cudaGetLastError());
+}
+
+extern "C" rf_status rf_residual(rf_ctx *ctx, const rf_grid *grid, const float *proj5, float eps,
+                                 const uint8_t *src, const float *T, float *res, float *max_abs,
+                                 void *stream) {
+  if (!ctx || !grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const long long n = (long long)grid->ny * grid->nx;
+  RecordArgs r;
+  r.ny = grid->ny;
+  r.nx = grid->nx;
+  r.h = grid->h;
+  r.eps = eps;
+  r.f = proj5;
+  r.src = src;
+  r.T = T;
+  r.id = nullptr;
+  r.w1 = nullptr;
+  r.dT = nullptr;
+  r.res = res;
+  r.max_abs = max_abs;
+  r.st = ctx->state;
+  if (max_abs) cudaMemsetAsync(max_abs, 0, sizeof(float), s);
+  cudaMemsetAsync(&ctx->state->max_res_bits, 0, sizeof(unsigned), s);
+  record_kernel<false><<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(r);
+  return cuda_status(cudaGetLastError());
+}

@@ -1,0 +1,100 @@
+// rf_sweep_common.cuh -- pieces shared by the band-pipelined line-sweep
+// kernels (forward solve and transposed-sweep adjoint): bounded waits, the
+// bounded grid barrier, tile geometry and direction mappings.
+#pragma once
+
+#include "rf_device.cuh"
+
+namespace rf {
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Per-launch control words (device): abort flag raised by any timed-out
+// wait so that every CTA leaves its loops.
+struct LaunchCtl {
+  DevState *st;
+  int *abort;
+  long long timeout_ns;
+};
+
+__device__ __forceinline__ void raise_timeout(const LaunchCtl &c) {
+  set_error(c.st, RF_ERR_TIMEOUT);
+  atomicExch(c.abort, 1);
+}
+
+// Spin until *p >= target; false (and a raised timeout) on expiry.
+__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target,
+                                         const LaunchCtl &c) {
+  if (ld_acquire_u32(p) >= target) return true;
+  const unsigned long long t0 = gtimer();
+  while (ld_acquire_u32(p) < target) {
+    if ((long long)(gtimer() - t0) > c.timeout_ns || ld_acquire_s32(c.abort)) {
+      raise_timeout(c);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// Bounded grid-wide barrier for a cooperative launch.  Every CTA calls it.
+__device__ __forceinline__ bool grid_sync(const LaunchCtl &c) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    DevState *st = c.st;
+    const unsigned g = ld_acquire_u32(&st->bar_gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      st_release_u32(&st->bar_gen, g + 1);
+    } else {
+      const unsigned long long t0 = gtimer();
+      while (ld_acquire_u32(&st->bar_gen) == g) {
+        if ((long long)(gtimer() - t0) > c.timeout_ns) {
+          raise_timeout(c);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    ok_s = ok && !ld_acquire_s32(c.abort);
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Global index of (line step s, line l) for sweep direction dir:
+// 0 columns +x, 1 rows +y, 2 columns -x, 3 rows -y.
+__device__ __forceinline__ long long gidx(int dir, int s, int l, int ny, int nx) {
+  int i, j;
+  if ((dir & 1) == 0) {
+    j = (dir == 0) ? s : nx - 1 - s;
+    i = l;
+  } else {
+    i = (dir == 1) ? s : ny - 1 - s;
+    j = l;
+  }
+  return (long long)i * nx + j;
+}
+
+// Tile offset (ds, dl) of neighbour n for direction dir.
+__device__ __forceinline__ void nb_tile_offset(int dir, int n, int &ds, int &dl) {
+  const int dx = nb_dx(n), dy = nb_dy(n);
+  switch (dir) {
+    case 0: ds = dx; dl = dy; break;
+    case 1: ds = dy; dl = dx; break;
+    case 2: ds = -dx; dl = dy; break;
+    default: ds = -dy; dl = dx; break;
+  }
+}
+
+}  // namespace rf

@@ -1,0 +1,185 @@
+"""GPU (CUDA, through the C ABI) vs FP64 oracle parity on seeded inputs.
+
+Sizes: the 64x64 and 512x512 workloads, a ragged multi-source grid that
+spans several bands and blocks with partial tails, and degenerate shapes.
+"""
+import numpy as np
+import pytest
+
+import rf_inputs as R
+from gpu_util import (FWD_TOL, GRAD_TOL, api, flip_mask, gpu_path, oracle_path, rel_l2, require_gpu, to_dev,
+                      torch)
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def ragged_case():
+    ny, nx = 203, 141  # several bands/blocks with partial tails
+    h = 1.0 / 202
+    return dict(raw=R.randers_fields(ny, nx, h, 8, seed=9, omega="field", omega_max=1.0),
+                src=R.random_sources(ny, nx, 3, seed=9), h=h, eps=1e-6, delta=0.3,
+                g=R.sparse_loss_grad(ny, nx, 0.05, seed=9))
+
+
+CASES = {"config1": R.config1, "ragged": ragged_case, "config2": R.config2}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    c = CASES[request.param]()
+    gpu = gpu_path(c["raw"], c["src"], c["h"], c["eps"], c["delta"], c["g"])
+    orc = oracle_path(c["raw"], c["src"], c["h"], c["eps"], c["delta"], c["g"])
+    return request.param, c, gpu, orc
+
+
+def test_projection_parity(case):
+    name, c, gpu, orc = case
+    same = gpu["clip"] == orc["clip"]
+    assert same.mean() > 0.999
+    assert np.allclose(gpu["proj"][:, same], orc["proj"][:, same], rtol=2e-6, atol=1e-7)
+
+
+def test_forward_parity(case):
+    name, c, gpu, orc = case
+    assert gpu["st_fwd"]["status"] == 0, gpu["st_fwd"]
+    assert gpu["st_fwd"]["converged"]
+    Tg, To = gpu["T"], orc["T"]
+    assert np.array_equal(np.isfinite(Tg), np.isfinite(To))
+    fin = np.isfinite(To)
+    tmax = To[fin].max()
+    err = np.abs(Tg[fin] - To[fin]).max()
+    assert err <= FWD_TOL * tmax, (name, err, tmax)
+    assert np.all(Tg[c["src"] == 1] == 0.0)
+
+
+def test_record_parity(case):
+    name, c, gpu, orc = case
+    flips, tmax = flip_mask(gpu, orc)
+    # near-ties (oracle margin < 1e-5 max T) may pick either stencil; outside
+    # them the GPU must name the oracle's stencil
+    hard = (gpu["rec_np"]["id"] != orc["rec"]["id"]) & (orc["rec"]["margin"] >= 1e-5 * tmax)
+    assert hard.mean() < 1e-3, (name, hard.sum(), flips.mean())
+    print(f"{name}: near-tie/flip fraction {flips.mean():.4f}, hard mismatches {int(hard.sum())}")
+    keep = ~flips
+    assert np.allclose(gpu["rec_np"]["w1"][keep], orc["rec"]["w1"][keep], atol=2e-3)
+    dTg, dTo = gpu["rec_np"]["dT"], orc["rec"]["dT"]
+    assert rel_l2(dTg, dTo, keep) < GRAD_TOL
+
+
+def test_gradient_parity(case):
+    name, c, gpu, orc = case
+    assert gpu["st_adj"]["status"] == 0, gpu["st_adj"]
+    flips, _ = flip_mask(gpu, orc)
+    keep = ~flips
+    e_lam = rel_l2(gpu["lam"], orc["lam"], keep)
+    e_proj = rel_l2(gpu["gproj"], orc["gproj"], keep)
+    e_raw = rel_l2(gpu["graw"], orc["graw"], keep)
+    assert e_proj < GRAD_TOL and e_raw < GRAD_TOL, (name, e_lam, e_proj, e_raw, flips.sum())
+
+
+def test_adjoint_kernel_on_oracle_record():
+    """The adjoint kernel alone, fed the oracle's record (cast to float32):
+    lambda and the contracted gradients must match the FP64 back-substitution
+    to float32 accuracy."""
+    c = R.config1()
+    orc = oracle_path(c["raw"], c["src"], c["h"], c["eps"], c["delta"], c["g"])
+    rec = api.Record(to_dev(orc["rec"]["id"], torch.uint8), to_dev(orc["rec"]["w1"], torch.float32),
+                     to_dev(orc["rec"]["dT"], torch.float32))
+    T = to_dev(orc["T"], torch.float32)
+    src = to_dev(c["src"], torch.uint8)
+    g = to_dev(np.where(np.isfinite(orc["T"]), c["g"], 0.0), torch.float32)
+    gproj, lam = api.rf_adjoint(src, T, rec, g)
+    st = api.Context.get(0).stats()
+    assert st["status"] == 0
+    assert rel_l2(lam.cpu().numpy(), orc["lam"]) < 1e-5
+    assert rel_l2(gproj.cpu().numpy(), orc["gproj"]) < 1e-5
+
+
+def test_residual_of_gpu_solution_is_small():
+    c = R.config2()
+    raw = to_dev(c["raw"], torch.float32)
+    src = to_dev(c["src"], torch.uint8)
+    proj, _ = api.rf_project(raw, c["eps"], c["delta"])
+    T, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], record=False)
+    mx = api.rf_residual(proj, c["eps"], src, c["h"], T)
+    tmax = T.max().item()
+    assert mx.item() <= 1e-6 * tmax
+    # independent check in FP64 at sampled nodes with the oracle's candidate set
+    Tn = T.cpu().numpy().astype(np.float64)
+    pr = proj.cpu().numpy().astype(np.float64)
+    res = O.residual(pr, c["src"], c["h"], c["eps"], Tn)
+    assert np.abs(res).max() <= 2e-6 * tmax
+
+
+@pytest.mark.parametrize("shape", [(1, 57), (57, 1), (2, 2), (33, 65), (130, 7)])
+def test_degenerate_shapes(shape):
+    ny, nx = shape
+    h = 0.1
+    raw = R.randers_fields(ny, nx, h, 4, seed=1, omega="unit", omega_scale=0.2)
+    src = R.point_sources(ny, nx, [(ny // 2, nx // 2)])
+    prj, _ = O.project(raw, 1e-6, 0.05)
+    To, _, _, _ = O.solve_gs(prj, src, h, 1e-6)
+    proj, _ = api.rf_project(to_dev(raw, torch.float32), 1e-6, 0.05)
+    T, _ = api.rf_sweep_forward(proj, 1e-6, to_dev(src, torch.uint8), h)
+    st = api.Context.get(0).stats()
+    assert st["status"] == 0 and st["converged"]
+    assert np.abs(T.cpu().numpy() - To).max() <= FWD_TOL * To.max()
+
+
+def test_no_source_and_all_sources():
+    ny, nx = 40, 50
+    raw = to_dev(R.randers_fields(ny, nx, 0.1, 4, seed=2), torch.float32)
+    proj, _ = api.rf_project(raw, 1e-6, 0.05)
+    ctx = api.Context.get(0)
+    T, _ = api.rf_sweep_forward(proj, 1e-6, torch.zeros((ny, nx), dtype=torch.uint8, device="cuda"), 0.1)
+    st = ctx.stats()
+    assert st["status"] == 6  # RF_ERR_NO_SOURCE
+    assert torch.isinf(T).all()
+    T, rec = api.rf_sweep_forward(proj, 1e-6, torch.ones((ny, nx), dtype=torch.uint8, device="cuda"), 0.1)
+    st = ctx.stats()
+    assert st["status"] == 0 and (T == 0).all() and (rec.id == 0).all()
+
+
+def test_nonfinite_input_is_reported():
+    ny, nx = 16, 16
+    raw = R.randers_fields(ny, nx, 0.1, 4, seed=2)
+    raw[3, 5, 5] = np.nan
+    api.rf_project(to_dev(raw, torch.float32), 1e-6, 0.05)
+    assert api.Context.get(0).stats()["status"] == 5  # RF_ERR_NONFINITE_INPUT
+
+
+def test_timeout_path_returns_cleanly():
+    """A zero wait bound makes the first unsatisfied device wait expire: the
+    launch must end with RF_ERR_TIMEOUT and leave the context usable."""
+    c = R.config2()
+    raw = to_dev(c["raw"], torch.float32)
+    src = to_dev(c["src"], torch.uint8)
+    ctx = api.Context(0)
+    proj, _ = api.rf_project(raw, c["eps"], c["delta"], ctx=ctx)
+    ctx.set_timeout(0)
+    api.rf_sweep_forward(proj, c["eps"], src, c["h"], record=False, ctx=ctx)
+    st = ctx.stats()
+    assert st["status"] == 4  # RF_ERR_TIMEOUT
+    ctx.set_timeout(2_000_000_000)
+    T, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], record=False, ctx=ctx)
+    st = ctx.stats()
+    assert st["status"] == 0 and st["converged"]
+
+
+@pytest.mark.parametrize("band,block", [(32, 8), (64, 32), (128, 16), (16, 16)])
+def test_band_and_block_shapes_agree(band, block):
+    c = ragged_case()
+    prj, _ = O.project(c["raw"], c["eps"], c["delta"])
+    To, _, _, _ = O.solve_gs(prj, c["src"], c["h"], c["eps"])
+    proj, _ = api.rf_project(to_dev(c["raw"], torch.float32), c["eps"], c["delta"])
+    T, _ = api.rf_sweep_forward(proj, c["eps"], to_dev(c["src"], torch.uint8), c["h"],
+                                opts=api.make_opts(band=band, block=block), record=False)
+    st = api.Context.get(0).stats()
+    assert st["status"] == 0 and st["converged"]
+    assert np.abs(T.cpu().numpy() - To).max() <= FWD_TOL * To.max()
