@@ -167,6 +167,34 @@ rf_status rf_record_stencils(rf_ctx *ctx, const rf_grid *grid,
                              const float *proj5, float eps, const uint8_t *src,
                              const float *T, rf_record *rec, void *stream);
 
+/* Forward solve that allocates nothing (the paper has no counterpart: this
+ * is a deployment variant of rf_sweep_forward without stencil record).
+ * For callers that cannot allocate device memory at solve time -- a host
+ * framework that has reserved the device's memory for its own allocator or
+ * enforces a memory budget, or a latency-critical loop that must not pay
+ * cudaMalloc's device-wide synchronisation.  It needs no rf_ctx: it runs on
+ * the calling thread's current device, with its scratch (second sweep
+ * buffer, progress and change flags, status word) in one fixed file-scope
+ * device array of about 4 MiB that every GPU loading the library keeps
+ * until the process exits.  It calls no cudaMalloc/cudaFree.
+ * Limits: ny * nx <= 1048576 nodes and opts->max_sweeps <= 1024; larger
+ * requests return RF_ERR_INVALID_ARG before any work is enqueued.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array, which keeps
+ * the previous call's contents (the call clears what must start at zero):
+ * calls whose work overlaps on the GPU race with each other, so serialise
+ * them (one stream, or events).
+ * Arguments as rf_sweep_forward (T: caller's device output, and warm-start
+ * input when opts->mode == RF_MODE_WARM).  stats: HOST pointer, nullable;
+ * when given the call synchronises `stream`, fills *stats and returns the
+ * device status; when NULL the call is asynchronous and returns after
+ * enqueuing. */
+rf_status rf_sweep_forward_static(const rf_grid *grid, const float *proj5,
+                                  float eps, const uint8_t *src,
+                                  const rf_opts *opts, float *T,
+                                  rf_stats *stats, void *stream);
+
 /* B7: residual r = T - min valid candidate(T) at every non-source node.
  * res (nullable): [ny*nx] per-node residual; max_abs (device float*,
  * nullable): max |r| over nodes with finite T. */

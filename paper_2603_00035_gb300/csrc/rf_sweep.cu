@@ -25,6 +25,7 @@
 // barrier every CTA reads it and stops at the first sweep that changed
 // nothing.  Every wait is bounded by the context's timeout.
 #include <algorithm>
+#include <mutex>
 
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
@@ -526,4 +527,134 @@ extern "C" rf_status rf_residual(rf_ctx *ctx, const rf_grid *grid, const float *
   cudaMemsetAsync(&ctx->state->max_res_bits, 0, sizeof(unsigned), s);
   record_kernel<false><<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(r);
   return cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// rf_sweep_forward_static: the forward solve without any allocation.
+//
+// Some callers cannot allocate device memory when they solve: a host
+// framework that has already reserved the device's memory for its own
+// caching allocator or enforces a memory budget, or a latency-critical loop
+// that must not pay cudaMalloc's implicit device-wide synchronisation.  This
+// entry point runs the same kernels as rf_sweep_forward, but its scratch --
+// the second T buffer of the ping-pong sweeps, the per-band progress tokens,
+// the per-sweep change flags and the device status word -- lives in one
+// file-scope __device__ array of fixed size, which every GPU that loads the
+// library holds until the process exits.  The caller still passes the
+// inputs and the output T.
+namespace {
+
+constexpr long long kStaticMaxNodes = 1LL << 20;  // ny * nx <= 1,048,576
+constexpr int kStaticMaxSweeps = 1024;
+constexpr int kStaticMaxBands = 4096;
+constexpr int kStaticMaxDevices = 64;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kStaticTOff = 0;
+constexpr size_t kStaticProgOff = align256(kStaticTOff + (size_t)kStaticMaxNodes * sizeof(float));
+constexpr size_t kStaticChgOff = align256(kStaticProgOff + (size_t)(kStaticMaxBands + 1) * sizeof(unsigned));
+constexpr size_t kStaticStateOff = align256(kStaticChgOff + (size_t)(kStaticMaxSweeps + 2) * sizeof(int));
+constexpr size_t kStaticBytes = align256(kStaticStateOff + sizeof(rf::DevState));
+
+std::mutex g_static_mu;
+void *g_static_addr[kStaticMaxDevices] = {};
+
+}  // namespace
+
+// Scratch of rf_sweep_forward_static (about 4 MiB per device).  In host code
+// this name is only a host-side stand-in: kernels receive the device address
+// obtained with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_rf_static_scratch[kStaticBytes];
+
+extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *proj5, float eps,
+                                             const uint8_t *src, const rf_opts *opts, float *T,
+                                             rf_stats *stats, void *stream) {
+  if (!grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
+  if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0};
+  if (opts) o = *opts;
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+    return RF_ERR_INVALID_ARG;
+  const int ny = grid->ny, nx = grid->nx;
+  const long long n = (long long)ny * nx;
+  // sizes beyond the fixed scratch are rejected before any work is enqueued
+  if (n > kStaticMaxNodes || o.max_sweeps > kStaticMaxSweeps) return RF_ERR_INVALID_ARG;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RF_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return RF_ERR_UNSUPPORTED;
+  unsigned char *base = nullptr;
+  {
+    // once per device, with that device current: the device address of the
+    // scratch array
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_rf_static_scratch) != cudaSuccess || !p) return RF_ERR_CUDA;
+      g_static_addr[dev] = p;
+    }
+    base = (unsigned char *)g_static_addr[dev];
+  }
+
+  rf_ctx planner;  // a stack object: only the device and SM count are used
+  planner.device = dev;
+  if (cudaDeviceGetAttribute(&planner.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RF_ERR_CUDA;
+  SweepPlan pl;
+  rf_status rs = plan_sweep(&planner, ny, nx, &o, &pl);
+  if (rs != RF_OK) return rs;
+  if (pl.grid > kStaticMaxBands) return RF_ERR_INVALID_ARG;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  float *tb = (float *)(base + kStaticTOff);
+  unsigned *progress = (unsigned *)(base + kStaticProgOff);
+  int *changed = (int *)(base + kStaticChgOff);
+  DevState *st = (DevState *)(base + kStaticStateOff);
+  // the array keeps the previous call's contents: clear what must start at 0
+  if (cudaMemsetAsync(progress, 0, sizeof(unsigned) * (pl.grid + 1), s) != cudaSuccess ||
+      cudaMemsetAsync(changed, 0, sizeof(int) * (o.max_sweeps + 2), s) != cudaSuccess ||
+      cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess)
+    return RF_ERR_CUDA;
+
+  int *has_src = changed + o.max_sweeps;
+  init_kernel<<<blocks_for(n, 256, planner.num_sms * 8), 256, 0, s>>>(T, src, n, o.mode == RF_MODE_WARM, st,
+                                                                        has_src);
+  check_source_kernel<<<1, 32, 0, s>>>(has_src, st);
+
+  SweepArgs a;
+  a.ny = ny;
+  a.nx = nx;
+  a.h = grid->h;
+  a.eps = eps;
+  a.f = proj5;
+  a.src = src;
+  a.Ta = T;
+  a.Tb = tb;
+  a.R = pl.R;
+  a.K = pl.K;
+  a.max_sweeps = o.max_sweeps;
+  a.tol = o.tol;
+  a.tok_stride = (unsigned)((std::max(ny, nx) + pl.K - 1) / pl.K + 1);
+  a.progress = progress;
+  a.changed = changed;
+  a.ctl.st = st;
+  a.ctl.abort = changed + o.max_sweeps + 1;
+  a.ctl.timeout_ns = 2000000000LL;
+  void *args[] = {&a};
+  if (cudaLaunchCooperativeKernel((const void *)sweep_kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, s) !=
+      cudaSuccess)
+    return RF_ERR_CUDA;
+  if (!stats) return RF_OK;
+  DevState h;
+  if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return RF_ERR_CUDA;
+  stats->status = h.status;
+  stats->sweeps = h.sweeps;
+  stats->converged = h.converged;
+  stats->adj_sweeps = 0;
+  stats->cell_updates = (int64_t)h.cell_updates;
+  stats->max_residual = 0.0f;
+  stats->pad = 0.0f;
+  return (rf_status)h.status;
 }
