@@ -119,7 +119,7 @@ const char *rf_status_string(rf_status s);
 
 /* ---- a1: feasibility projection -----------------------------------------
  * Paper: App. B "Feasibility Projections" (the G^-1-norm of b) and the
- * spec form M = L L^T + eps I.  For each node:
+ * metric in factor form M = L L^T + eps I.  For each node:
  *   n = |w|_{M^-1} = sqrt((wx^2 M22 - 2 wx wy M12 + wy^2 M11) / det M),
  *   w_out = w * min(1, (1 - delta) / n);
  * L passes through.  raw5, proj5: 5-plane arrays (may alias only if equal);

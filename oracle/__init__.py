@@ -88,7 +88,7 @@ def cell_eval(Tn, h, g11, g12, g22, wx, wy):
 
 
 def project(raw5, eps, delta):
-    """Feasibility projection (App. B; spec form M = L L^T + eps I).
+    """Feasibility projection (App. B; metric in factor form M = L L^T + eps I).
 
     raw5: array (5, ...) of L11, L21, L22, wx, wy.  Returns (proj5, clip)
     where proj5 = (L11, L21, L22, wpx, wpy).

@@ -214,7 +214,7 @@ void orc_cell_eval(const double *Tn, double h, double g11, double g12,
 
 /* ------------------------------------------------------------------ */
 /*
- * Feasibility projection (spec form; w-norm formula of App. B):
+ * Feasibility projection (metric in factor form; w-norm formula of App. B):
  *   M = L L^T + eps I,   n = |w|_{M^-1} = sqrt((wx^2 M22 - 2 wx wy M12 +
  *   wy^2 M11) / det M),  w_out = w * min(1, c / n),  c = 1 - delta.
  * The boundary n == c counts as unclipped.  L passes through unchanged.

@@ -1,6 +1,6 @@
 // rf_project.cu -- a1 feasibility projection and a9 its backward.
 // Paper: App. B "Feasibility Projections" (|b|_{G^-1} via the closed-form
-// 2x2 inverse); spec form M = L L^T + eps I, w scaled to
+// 2x2 inverse); factor form M = L L^T + eps I, w scaled to
 // |w|_{M^-1} <= 1 - delta.  Elementwise and HBM-bound: 20 B read + 8 B
 // (+1 B clip) written per node forward; 40 B read + 20 B written backward.
 #include "rf_ctx.h"

@@ -2,7 +2,7 @@
 the whole CUDA path and the FP64 oracle on the same seeded inputs, and the
 tolerance rules.
 
-Tolerances (spec parity bar):
+Tolerances (the parity bar):
 * forward: max |T_gpu - T_oracle| <= 1e-4 * max T over reached nodes, and
   the reached set identical;
 * gradients: relative L2 <= 1e-3 over nodes outside the flip set;
