@@ -35,7 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "forward+adjoint solves/s at 2048x2048"
 UNIT = "solves/s"
 ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-update
-LAUNCHES_PER_STEP = 7      # project, init, source check, sweep, record, adjoint, project backward
+# kernels of ours per step: project, init, source check, sweep, record, project backward, plus the
+# adjoint's own kernels (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not counted)
+LAUNCHES_PER_STEP = {"sweep": 7, "ordered": 9}
 
 
 def parse():
@@ -45,7 +47,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=2048)
-    p.add_argument("--algo", default="sweep", choices=["sweep", "ordered"])
+    p.add_argument("--algo", default="ordered", choices=["sweep", "ordered"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -300,9 +302,13 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     if names[dom] == "sweep_forward":
         bytes_per_launch = ALG_BYTES_PER_UPDATE * cell_updates
-    elif names[dom] == "adjoint":
+    elif names[dom] == "adjoint" and args.algo == "sweep":
         # per node per adjoint sweep: id 1 B + w1 4 B + lambda read 4 B + write 4 B + g 4 B + T 4 B
         bytes_per_launch = 21 * adj_sweeps * n * n + 44 * n * n
+    elif names[dom] == "adjoint":
+        # ordered: sort keys+values (2 x 4 B in, 2 x 4 B out) + per node id 1 + w1 4 + state 8 r + 8 w
+        # + g 4 + T 4 + dT 20 + grad 20
+        bytes_per_launch = (16 + 69) * n * n
     else:
         bytes_per_launch = 60 * n * n
     achieved = bytes_per_launch / (phase_ms[dom] / 1e3) / 1e9
@@ -312,7 +318,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(n),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP[args.algo] * args.steps,
             "clocks": sampler.summary(),
             "solver": {"sweeps": sweeps, "adj_sweeps": adj_sweeps, "cell_updates": cell_updates,
                        "gcell_updates_per_s": cell_updates / (phase_ms[1] / 1e3) / 1e9,

@@ -15,6 +15,8 @@
 // loop; zero at sources and unreached nodes) and the optional lambda.
 #include <algorithm>
 
+#include <cub/device/device_radix_sort.cuh>
+
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
 
@@ -55,6 +57,8 @@ __device__ __forceinline__ float child_weight(uint8_t id, float w1, int back) {
   return 0.0f;
 }
 
+constexpr int kAdjLanes = 4;  // lanes per node: lane q gathers neighbours 2q, 2q+1
+
 __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
   extern __shared__ float smem[];
   const int R = a.R, K = a.K, ext = R + 2 * K, W = ext + 2, P = W | 1, EP = ext | 1;
@@ -66,6 +70,8 @@ __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
   __shared__ int s_ok, s_any;
 
   const int tid = threadIdx.x, nth = blockDim.x, b = blockIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+  const int cell = tid / kAdjLanes, q = tid % kAdjLanes;
   const long long plane = (long long)a.ny * a.nx;
   float *cur = a.La, *nxt = a.Lb;
   int sweep = 0, converged = 0;
@@ -80,6 +86,9 @@ __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
     const int nblk = (S + K - 1) / K;
     const unsigned base = (unsigned)sweep * a.tok_stride;
     int local_changed = 0;
+    int nds[2], ndl[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) nb_tile_offset(dir, 2 * q + u, nds[u], ndl[u]);
     if (b < nb && !abort) {
       const int l0 = b * R, line0 = l0 - K - 1;
       for (int kb = 0; kb < nblk; ++kb) {
@@ -97,23 +106,27 @@ __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
           abort = true;
           break;
         }
-        const int rows = K + 2;
-        for (int f = tid; f < rows * W; f += nth) {
-          int ts, tl;
-          if (col) { tl = f / rows; ts = f - tl * rows; }
-          else     { ts = f / W;    tl = f - ts * W; }
-          const int s = s0 - 1 + ts, l = line0 + tl;
-          float v = 0.0f, w = 0.0f;
-          uint8_t d = 0;
-          if (s >= 0 && s < S && l >= 0 && l < L) {
-            const long long gi = gidx(dir, s, l, a.ny, a.nx);
-            v = __ldcg(cur + gi);
-            w = __ldg(a.w1 + gi);
-            d = __ldg(a.id + gi);
+        // stage lambda before the sweep, w1 and ids on (K+2) x W; warps walk
+        // the non-contiguous direction, lanes the contiguous one
+        {
+          const int n_outer = col ? W : K + 2, n_inner = col ? K + 2 : W;
+          for (int o = warp; o < n_outer; o += nwarps) {
+            for (int in = lane; in < n_inner; in += 32) {
+              const int ts = col ? in : o, tl = col ? o : in;
+              const int s = s0 - 1 + ts, l = line0 + tl;
+              float v = 0.0f, w = 0.0f;
+              uint8_t d = 0;
+              if (s >= 0 && s < S && l >= 0 && l < L) {
+                const long long gi = gidx(dir, s, l, a.ny, a.nx);
+                v = __ldcg(cur + gi);
+                w = __ldg(a.w1 + gi);
+                d = __ldg(a.id + gi);
+              }
+              old[ts * P + tl] = v;
+              ww[ts * P + tl] = w;
+              ids[ts * P + tl] = d;
+            }
           }
-          old[ts * P + tl] = v;
-          ww[ts * P + tl] = w;
-          ids[ts * P + tl] = d;
         }
         for (int tl = tid; tl < W; tl += nth) {
           const int s = s0 - 1, l = line0 + tl;
@@ -124,17 +137,20 @@ __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
           }
           nw[tl] = v;
         }
-        for (int f = tid; f < K * ext; f += nth) {
-          int t, e;
-          if (col) { e = f / K; t = f - e * K; }
-          else     { t = f / ext; e = f - t * ext; }
-          const int s = s0 + t, l = l0 - K + e;
-          float v = 0.0f;
-          if (s < S && l >= 0 && l < L) {
-            const long long gi = gidx(dir, s, l, a.ny, a.nx);
-            v = (__ldg(a.T + gi) < kInf) ? __ldg(a.g + gi) : 0.0f;
+        {
+          const int n_outer = col ? ext : K, n_inner = col ? K : ext;
+          for (int o = warp; o < n_outer; o += nwarps) {
+            for (int in = lane; in < n_inner; in += 32) {
+              const int t = col ? in : o, e = col ? o : in;
+              const int s = s0 + t, l = l0 - K + e;
+              float v = 0.0f;
+              if (s < S && l >= 0 && l < L) {
+                const long long gi = gidx(dir, s, l, a.ny, a.nx);
+                v = (__ldg(a.T + gi) < kInf) ? __ldg(a.g + gi) : 0.0f;
+              }
+              gg[t * EP + e] = v;
+            }
           }
-          gg[t * EP + e] = v;
         }
         __syncthreads();
         for (int t = tid; t < K; t += nth) {
@@ -144,36 +160,50 @@ __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
         for (int t = 0; t < K; ++t) {
           const int s = s0 + t;
           if (s >= S) break;
-          if (tid < ext) {
-            const int e = tid, tl = e + 1, l = l0 - K + e;
-            float lnew = 0.0f;
-            if (l >= 0 && l < L) {
-              const float lold = old[(t + 1) * P + tl];
-              float acc = gg[t * EP + e];
+          const int e = cell, tl = e + 1, l = l0 - K + e;
+          const bool live = (e < ext) && (l >= 0) && (l < L);
+          float part = 0.0f;
+          if (live) {
 #pragma unroll
-              for (int n = 0; n < 8; ++n) {
-                int ds, dl;
-                nb_tile_offset(dir, n, ds, dl);
-                const int r = t + 1 + ds, cidx = tl + dl;
-                const float wq = child_weight(ids[r * P + cidx], ww[r * P + cidx], (n + 4) & 7);
-                if (wq != 0.0f) {
-                  const float lq = (ds < 0) ? nw[t * P + cidx] : old[r * P + cidx];
-                  acc = fmaf(wq, lq, acc);
-                }
+            for (int u = 0; u < 2; ++u) {
+              const int r = t + 1 + nds[u], cidx = tl + ndl[u];
+              const float wq = child_weight(ids[r * P + cidx], ww[r * P + cidx], (2 * q + u + 4) & 7);
+              if (wq != 0.0f) {
+                const float lq = (nds[u] < 0) ? nw[t * P + cidx] : old[r * P + cidx];
+                part = fmaf(wq, lq, part);
               }
-              lnew = acc;
+            }
+          }
+          // fixed-order tree: ((q0 + q1) + (q2 + q3)), then + g
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          if (q == 0 && e < ext) {
+            float lnew = 0.0f;
+            if (live) {
+              const float lold = old[(t + 1) * P + tl];
+              lnew = gg[t * EP + e] + part;
               if (e >= K && e < K + R) local_changed |= (__float_as_uint(lnew) != __float_as_uint(lold));
             }
             nw[(t + 1) * P + tl] = lnew;
           }
           __syncthreads();
         }
-        for (int f = tid; f < K * R; f += nth) {
-          int t, e;
-          if (col) { e = f / K; t = f - e * K; }
-          else     { t = f / R; e = f - t * R; }
-          const int s = s0 + t, l = l0 + e;
-          if (s < S && l < L) nxt[gidx(dir, s, l, a.ny, a.nx)] = nw[(t + 1) * P + K + 1 + e];
+        if (col) {
+          for (int e = warp; e < R; e += nwarps) {
+            const int l = l0 + e;
+            for (int t = lane; t < K; t += 32) {
+              const int s = s0 + t;
+              if (s < S && l < L) nxt[gidx(dir, s, l, a.ny, a.nx)] = nw[(t + 1) * P + K + 1 + e];
+            }
+          }
+        } else {
+          for (int t = warp; t < K; t += nwarps) {
+            const int s = s0 + t;
+            for (int e = lane; e < R; e += 32) {
+              const int l = l0 + e;
+              if (s < S && l < L) nxt[gidx(dir, s, l, a.ny, a.nx)] = nw[(t + 1) * P + K + 1 + e];
+            }
+          }
         }
         __syncthreads();
         if (tid == 0) {
@@ -213,9 +243,213 @@ __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
   }
 }
 
+
+// ---- RF_ADJ_ORDERED: radix sort on T, then a dependency-ordered gather ----
+//
+// Children always have a strictly larger T than their parents (the
+// causality test of the two-point update; F > 0 for the one-point update),
+// so processing nodes in decreasing T finishes every child before its
+// parents (Alg. 2, "sort nodes by decreasing T").  A CUB radix sort orders
+// the nodes; a persistent kernel then hands out the sorted positions in
+// warp-sized tickets.  Each lane waits (bounded) until every child named by
+// the record has published its multiplier, gathers them in a fixed
+// neighbour order (no atomics on lambda), and publishes its own multiplier
+// and the epoch of this launch in one 64-bit release store.  The latency
+// chain is the depth of the stencil DAG, not a sweep count.
+
+__global__ void ordered_keys_kernel(const float *T, unsigned *keys, unsigned *vals, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const float t = T[p];
+    // ascending key = decreasing T; unreached (+inf) nodes first (key 0)
+    keys[p] = (t < kInf) ? ~__float_as_uint(t) : 0u;
+    vals[p] = (unsigned)p;
+  }
+}
+
+struct OrderedArgs {
+  int ny, nx;
+  const uint8_t *src;
+  const float *T;
+  const uint8_t *id;
+  const float *w1;
+  const float *dT;
+  const float *g;
+  const unsigned *order;  // node indices by decreasing T
+  unsigned long long *state;  // (epoch << 32) | lambda bits
+  unsigned epoch;
+  unsigned *ticket;
+  float *grad;
+  float *lam_out;
+  LaunchCtl ctl;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long n = (long long)a.ny * a.nx;
+  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  while (true) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(a.ticket, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= n || ld_acquire_s32(a.ctl.abort)) break;
+    const long long pos = (long long)base + lane;
+    bool done = pos >= n;
+    long long p = -1;
+    unsigned cmask = 0;  // children among the 8 neighbours
+    float cw[8];
+    float gsum = 0.0f;
+    int pi = 0, pj = 0;
+    if (!done) {
+      p = a.order[pos];
+      pi = (int)(p / a.nx);
+      pj = (int)(p - (long long)pi * a.nx);
+      const float tp = a.T[p];
+      if (!(tp < kInf)) {
+        // unreached: no residual, no children
+        st_release_u64(&a.state[p], tag);
+        done = true;
+      } else {
+        gsum = a.g[p];
+      }
+    }
+#pragma unroll
+    for (int nb = 0; nb < 8; ++nb) {
+      cw[nb] = 0.0f;
+      const int ii = pi + nb_dy(nb), jj = pj + nb_dx(nb);
+      if (!done && ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx) {
+        const long long qn = (long long)ii * a.nx + jj;
+        cw[nb] = child_weight(a.id[qn], a.w1[qn], (nb + 4) & 7);
+        if (cw[nb] != 0.0f) cmask |= 1u << nb;
+      }
+    }
+    const unsigned long long t0 = gtimer();
+    while (!__all_sync(0xffffffffu, done)) {
+      if (!done) {
+        bool ready = true;
+        float acc = gsum;
+#pragma unroll
+        for (int nb = 0; nb < 8; ++nb) {
+          if (cmask & (1u << nb)) {
+            const long long qn = (long long)(pi + nb_dy(nb)) * a.nx + (pj + nb_dx(nb));
+            const unsigned long long v = ld_acquire_u64(&a.state[qn]);
+            ready = ready && ((v & 0xffffffff00000000ull) == tag);
+            acc = fmaf(cw[nb], __uint_as_float((unsigned)v), acc);
+          }
+        }
+        if (ready) {
+          st_release_u64(&a.state[p], tag | __float_as_uint(acc));
+          const bool act = a.id[p] != 0 && !a.src[p];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) a.grad[c * n + p] = act ? acc * a.dT[c * n + p] : 0.0f;
+          if (a.lam_out) a.lam_out[p] = acc;
+          done = true;
+        } else if ((long long)(gtimer() - t0) > a.ctl.timeout_ns || ld_acquire_s32(a.ctl.abort)) {
+          raise_timeout(a.ctl);
+          done = true;
+        }
+      }
+    }
+  }
+  // unreached nodes: zero gradient and lambda
+}
+
+__global__ void ordered_unreached_kernel(const float *T, float *grad, float *lam, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (!(T[p] < kInf)) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) grad[c * n + p] = 0.0f;
+      if (lam) lam[p] = 0.0f;
+    }
+  }
+}
+
 }  // namespace rf
 
 using namespace rf;
+
+namespace {
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+rf_status adjoint_ordered(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, const float *T,
+                          const rf_record *rec, const float *dLdT, float *dLdproj5, float *lambda,
+                          cudaStream_t s) {
+  ctx->last_stream = s;
+  const long long n = (long long)grid->ny * grid->nx;
+  // scratch: keys in/out, values in/out, ticket, abort flag, CUB temp
+  size_t temp_bytes = 0;
+  if (cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (unsigned *)nullptr, (unsigned *)nullptr,
+                                      (unsigned *)nullptr, (unsigned *)nullptr, (int)n, 0, 32, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+  const size_t arr = align_up((size_t)n * sizeof(unsigned));
+  const size_t need = 4 * arr + 256 + align_up(temp_bytes);
+  rf_status rs;
+  if ((rs = ensure((unsigned char **)&ctx->scratch, &ctx->scratch_cap, need)) != RF_OK) return rs;
+  unsigned char *base = (unsigned char *)ctx->scratch;
+  unsigned *kin = (unsigned *)base, *kout = (unsigned *)(base + arr), *vin = (unsigned *)(base + 2 * arr),
+           *vout = (unsigned *)(base + 3 * arr);
+  unsigned *ctl_words = (unsigned *)(base + 4 * arr);  // [0] ticket, [1] abort
+  void *temp = base + 4 * arr + 256;
+  // per-node state words tagged with a launch epoch (cleared on first use
+  // and whenever the epoch counter wraps)
+  const bool fresh = ctx->adj_state_cap < (size_t)n || !ctx->adj_state;
+  if ((rs = ensure(&ctx->adj_state, &ctx->adj_state_cap, (size_t)n)) != RF_OK) return rs;
+  if (fresh || ctx->adj_epoch == 0xffffffffu) {
+    if (cudaMemsetAsync(ctx->adj_state, 0, sizeof(unsigned long long) * ctx->adj_state_cap, s) != cudaSuccess)
+      return RF_ERR_CUDA;
+    ctx->adj_epoch = 0;
+  }
+  const unsigned epoch = ++ctx->adj_epoch;
+  if (cudaMemsetAsync(ctl_words, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return RF_ERR_CUDA;
+
+  ordered_keys_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, kin, vin, n);
+  if (cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, (int)n, 0, 32, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+
+  OrderedArgs a;
+  a.ny = grid->ny;
+  a.nx = grid->nx;
+  a.src = src;
+  a.T = T;
+  a.id = rec->id;
+  a.w1 = rec->w1;
+  a.dT = rec->dT;
+  a.g = dLdT;
+  a.order = vout;
+  a.state = ctx->adj_state;
+  a.epoch = epoch;
+  a.ticket = ctl_words;
+  a.grad = dLdproj5;
+  a.lam_out = lambda;
+  a.ctl.st = ctx->state;
+  a.ctl.abort = (int *)(ctl_words + 1);
+  a.ctl.timeout_ns = ctx->timeout_ns;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ordered_gather_kernel, 256, 0) != cudaSuccess ||
+      per_sm < 1)
+    return RF_ERR_CUDA;
+  // every warp that takes a ticket must be resident: a cooperative launch
+  // guarantees it
+  void *args[] = {&a};
+  if (cudaLaunchCooperativeKernel((const void *)ordered_gather_kernel, dim3(per_sm * ctx->num_sms), dim3(256),
+                                  args, 0, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+  ordered_unreached_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, dLdproj5, lambda, n);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
 
 extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, const float *T,
                                 const rf_record *rec, const float *dLdT, float *dLdproj5, float *lambda,
@@ -223,8 +457,9 @@ extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t 
   if (!ctx || !grid_ok(grid) || !src || !T || !rec || !rec->id || !rec->w1 || !rec->dT || !dLdT ||
       !dLdproj5)
     return RF_ERR_INVALID_ARG;
-  if (algo != RF_ADJ_SWEEP) return RF_ERR_UNSUPPORTED;
+  if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED) return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  if (algo == RF_ADJ_ORDERED) return adjoint_ordered(ctx, grid, src, T, rec, dLdT, dLdproj5, lambda, (cudaStream_t)stream);
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
   const int ny = grid->ny, nx = grid->nx;
@@ -238,7 +473,7 @@ extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t 
   int grid_ = 0, threads = 0;
   size_t smem = 0;
   for (int attempt = 0; attempt < 8; ++attempt) {
-    threads = ((R + 2 * K + 31) / 32) * 32;
+    threads = kAdjLanes * (R + 2 * K);
     smem = adj_smem_bytes(R, K);
     if (threads > 1024 || (long long)smem > dev_max_smem) return RF_ERR_UNSUPPORTED;
     cudaFuncSetAttribute(adjoint_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -36,6 +36,7 @@ extern "C" rf_status rf_ctx_destroy(rf_ctx *c) {
   cudaFree(c->tbuf);
   cudaFree(c->lbuf);
   cudaFree(c->scratch);
+  cudaFree(c->adj_state);
   delete c;
   return RF_OK;
 }

@@ -27,6 +27,9 @@ struct rf_ctx {
   size_t lbuf_cap = 0;
   void *scratch = nullptr;  // adjoint (ordered): sort keys/values/temp
   size_t scratch_cap = 0;
+  unsigned long long *adj_state = nullptr;  // adjoint (ordered): (epoch << 32 | lambda bits)
+  size_t adj_state_cap = 0;
+  unsigned adj_epoch = 0;  // launch counter tagging adj_state words
 };
 
 namespace rf {

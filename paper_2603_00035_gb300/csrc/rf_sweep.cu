@@ -48,36 +48,56 @@ struct SweepArgs {
   LaunchCtl ctl;
 };
 
-// Tile geometry of one CTA (all in elements).
-struct Tile {
-  int R, K, ext, W, P, EP;
-  __device__ Tile(int R_, int K_) : R(R_), K(K_) {
-    ext = R + 2 * K;
-    W = ext + 2;
-    P = W | 1;  // odd pitch: conflict-free column-major fills
-    EP = ext | 1;
-  }
-};
+// Lanes per node in the line-step loop: lane q of a node evaluates the
+// two-point candidates of stencils 2q, 2q+1 and the one-point candidates of
+// neighbours 2q, 2q+1; a two-level shuffle takes the minimum.
+constexpr int kLanes = 4;
+constexpr int kMaxExt = 128;    // R + 2K <= 128  ->  <= 512 threads
+constexpr int kMaxTabPer = 8;   // node tables staged per thread per block (K/4)
+constexpr int kMaxOldPer = 12;  // old-T values staged per thread per block
 
 __host__ __device__ inline size_t sweep_smem_bytes(int R, int K) {
   const int ext = R + 2 * K, W = ext + 2, P = W | 1, EP = ext | 1;
-  size_t fl = (size_t)(K + 2) * P + (size_t)(K + 1) * P + 5 * (size_t)K * EP;
+  size_t fl = (size_t)(K + 2) * P + (size_t)(K + 1) * P + (size_t)kTabSize * K * EP;
   return fl * sizeof(float) + (size_t)K * EP;
 }
 
-__global__ void __launch_bounds__(1024) sweep_kernel(SweepArgs a) {
+__host__ __device__ inline int sweep_threads(int R, int K) { return kLanes * (R + 2 * K); }
+
+// Shapes the kernel accepts: K a power of two <= 32, R >= K, R + 2K <= 128,
+// and the staged values per thread within the register budget.
+__host__ inline bool sweep_shape_ok(int R, int K) {
+  if (K < 4 || K > 32 || (K & (K - 1)) || R < K || R + 2 * K > kMaxExt) return false;
+  const int nth = sweep_threads(R, K), W = R + 2 * K + 2;
+  return (K * (R + 2 * K) + nth - 1) / nth <= kMaxTabPer && ((K + 2) * W + nth - 1) / nth <= kMaxOldPer;
+}
+
+__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
   extern __shared__ float smem[];
-  const Tile tg(a.R, a.K);
-  const int R = tg.R, K = tg.K, ext = tg.ext, W = tg.W, P = tg.P, EP = tg.EP;
-  float *old = smem;                      // (K+2) x P
-  float *nw = old + (size_t)(K + 2) * P;  // (K+1) x P
-  float *fl = nw + (size_t)(K + 1) * P;   // 5 x K x EP
-  uint8_t *sm = (uint8_t *)(fl + (size_t)5 * K * EP);  // K x EP
+  const int R = a.R, K = a.K, ext = R + 2 * K, W = ext + 2, P = W | 1, EP = ext | 1;
+  float *old = smem;                                  // (K+2) x P  T before the sweep
+  float *nw = old + (size_t)(K + 2) * P;              // (K+1) x P  T of this sweep
+  float *tb = nw + (size_t)(K + 1) * P;               // kTabSize x K x EP node tables
+  uint8_t *sm = (uint8_t *)(tb + (size_t)kTabSize * K * EP);  // K x EP source flags
+  const int TS = K * EP;                              // table plane stride
   __shared__ int s_ok;
   __shared__ int s_any;
 
   const int tid = threadIdx.x, nth = blockDim.x, b = blockIdx.x;
+  const int cell = tid / kLanes, q = tid % kLanes;
+  const int logK = __ffs(K) - 1;
   const long long plane = (long long)a.ny * a.nx;
+  const int n_tab = K * ext, n_old = (K + 2) * W;
+
+  // per-lane table offsets (fixed for the whole launch)
+  const int n0 = 2 * q, n1 = 2 * q + 1, n2 = (2 * q + 2) & 7;
+  const int offL0 = (TAB_LEN + len_class(n0)) * TS, offL1 = (TAB_LEN + len_class(n1)) * TS,
+            offL2 = (TAB_LEN + len_class(n2)) * TS;
+  const int offW0 = (TAB_WM + (n0 & 3)) * TS, offW1 = (TAB_WM + (n1 & 3)) * TS, offW2 = (TAB_WM + (n2 & 3)) * TS;
+  const float sg0 = n0 < 4 ? 1.0f : -1.0f, sg1 = n1 < 4 ? 1.0f : -1.0f, sg2 = n2 < 4 ? 1.0f : -1.0f;
+  const bool xs = (q & 1) != 0;  // stencils 2q, 2q+1 differ along x for q = 1, 3
+  const int offLx = (TAB_LEN + (xs ? 0 : 1)) * TS, offInv = (xs ? TAB_IAX : TAB_IAY) * TS, offDet = TAB_DET * TS;
+
   float *cur = a.Ta, *nxt = a.Tb;
   int sweep = 0;
   int converged = 0;
@@ -92,13 +112,77 @@ __global__ void __launch_bounds__(1024) sweep_kernel(SweepArgs a) {
     const int nblk = (S + K - 1) / K;
     const unsigned base = (unsigned)sweep * a.tok_stride;
     int local_changed = 0;
+    // tile offsets of this lane's three neighbours 2q, 2q+1, 2q+2
+    int nds[3], ndl[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) nb_tile_offset(dir, (2 * q + u) & 7, nds[u], ndl[u]);
+    // staging lists of this thread (tile coordinates packed as lo | hi << 8):
+    // consecutive threads take consecutive memory (steps for column sweeps,
+    // lines for row sweeps)
+    int tabidx[kMaxTabPer], oldidx[kMaxOldPer];
+#pragma unroll
+    for (int j = 0; j < kMaxTabPer; ++j) {
+      const int f = tid + j * nth;
+      int t = 0, e = 0;
+      if (col) { e = f >> logK; t = f & (K - 1); }
+      else     { t = f / ext;   e = f - t * ext; }
+      tabidx[j] = (f < n_tab) ? (t | (e << 8)) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxOldPer; ++j) {
+      const int f = tid + j * nth;
+      int ts = 0, tl = 0;
+      if (col) { tl = f / (K + 2); ts = f - tl * (K + 2); }
+      else     { ts = f / W;       tl = f - ts * W; }
+      oldidx[j] = (f < n_old) ? (ts | (tl << 8)) : -1;
+    }
 
     if (b < nb && !abort) {
       const int l0 = b * R;
       const int line0 = l0 - K - 1;  // global line of tile column 0
+      float rv[kMaxTabPer][5];
+      uint8_t sv[kMaxTabPer];
+      float ov[kMaxOldPer];
+      // issue the (neighbour-independent) loads of the block starting at s0
+      auto prefetch = [&](int s0) {
+#pragma unroll
+        for (int j = 0; j < kMaxTabPer; ++j) {
+          const int t = tabidx[j] & 255, e = tabidx[j] >> 8;
+          const int s = s0 + t, l = l0 - K + e;
+          const bool ok = tabidx[j] >= 0 && s < S && l >= 0 && l < L;
+          const long long g = ok ? gidx(dir, s, l, a.ny, a.nx) : 0;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) rv[j][c] = ok ? __ldg(a.f + c * plane + g) : 1.0f;
+          sv[j] = ok ? a.src[g] : (uint8_t)0;
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxOldPer; ++j) {
+          const int ts = oldidx[j] & 255, tl = oldidx[j] >> 8;
+          const int s = s0 - 1 + ts, l = line0 + tl;
+          const bool ok = oldidx[j] >= 0 && s >= 0 && s < S && l >= 0 && l < L;
+          ov[j] = ok ? __ldcg(cur + gidx(dir, s, l, a.ny, a.nx)) : kInf;
+        }
+      };
+      prefetch(0);
       for (int kb = 0; kb < nblk; ++kb) {
         const int s0 = kb * K;
-        // 1. neighbours must have published block kb-1 of this sweep
+        // 1. node tables, source flags and T-before-sweep of this block
+#pragma unroll
+        for (int j = 0; j < kMaxTabPer; ++j) {
+          if (tabidx[j] < 0) continue;
+          const int t = tabidx[j] & 255, e = tabidx[j] >> 8;
+          float tab[kTabSize];
+          node_tab(rv[j][0], rv[j][1], rv[j][2], rv[j][3], rv[j][4], a.h, a.eps, tab);
+#pragma unroll
+          for (int c = 0; c < kTabSize; ++c) tb[c * TS + t * EP + e] = tab[c];
+          sm[t * EP + e] = sv[j];
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxOldPer; ++j) {
+          if (oldidx[j] < 0) continue;
+          old[(oldidx[j] & 255) * P + (oldidx[j] >> 8)] = ov[j];
+        }
+        // 2. neighbours must have published block kb-1 of this sweep
         if (tid == 0) {
           int ok = 1;
           if (kb > 0) {
@@ -112,90 +196,85 @@ __global__ void __launch_bounds__(1024) sweep_kernel(SweepArgs a) {
           abort = true;
           break;
         }
-        // 2. stage the tile: T before the sweep for steps s0-1..s0+K ...
-        const int rows_old = K + 2;
-        for (int f = tid; f < rows_old * W; f += nth) {
-          int ts, tl;
-          if (col) { tl = f / rows_old; ts = f - tl * rows_old; }
-          else     { ts = f / W;        tl = f - ts * W; }
-          const int s = s0 - 1 + ts, l = line0 + tl;
-          float v = kInf;
-          if (s >= 0 && s < S && l >= 0 && l < L) v = __ldcg(cur + gidx(dir, s, l, a.ny, a.nx));
-          old[ts * P + tl] = v;
-        }
-        // ... this sweep's values of step s0-1 (published by the neighbours)
+        // 3. this sweep's step s0-1 as published by the neighbours (halo
+        // lines) and by this CTA (inner lines); edge columns keep old values
         for (int tl = tid; tl < W; tl += nth) {
           const int s = s0 - 1, l = line0 + tl;
           float v = kInf;
           if (s >= 0 && l >= 0 && l < L) {
             const bool halo_ok = (tl >= 1 && tl <= ext);
-            v = halo_ok ? __ldcg(nxt + gidx(dir, s, l, a.ny, a.nx))
-                        : __ldcg(cur + gidx(dir, s, l, a.ny, a.nx));
+            v = halo_ok ? __ldcg(nxt + gidx(dir, s, l, a.ny, a.nx)) : __ldcg(cur + gidx(dir, s, l, a.ny, a.nx));
           }
           nw[tl] = v;
         }
-        // ... and the fields + source flags of the K x ext computed nodes
-        for (int f = tid; f < K * ext; f += nth) {
-          int t, e;
-          if (col) { e = f / K; t = f - e * K; }
-          else     { t = f / ext; e = f - t * ext; }
-          const int s = s0 + t, l = l0 - K + e;
-          if (s < S && l >= 0 && l < L) {
-            const long long g = gidx(dir, s, l, a.ny, a.nx);
-#pragma unroll
-            for (int c = 0; c < 5; ++c) fl[(size_t)c * K * EP + t * EP + e] = __ldg(a.f + c * plane + g);
-            sm[t * EP + e] = a.src[g];
-          }
-        }
-        __syncthreads();
-        // edge columns of the new tile (never computed): reuse old values
         for (int t = tid; t < K; t += nth) {
           nw[(t + 1) * P] = old[(t + 1) * P];
           nw[(t + 1) * P + W - 1] = old[(t + 1) * P + W - 1];
         }
-        // 3. K line steps, one parallel front each
+        __syncthreads();
+        // 4. K line steps, one parallel front each.  At step t only nodes
+        // e in [t+1, ext-1-t) can still influence the inner lines.
         for (int t = 0; t < K; ++t) {
           const int s = s0 + t;
           if (s >= S) break;
-          if (tid < ext) {
-            const int e = tid, tl = e + 1, l = l0 - K + e;
-            float tnew = kInf;
-            if (l >= 0 && l < L) {
-              const float told = old[(t + 1) * P + tl];
-              if (sm[t * EP + e]) {
-                tnew = 0.0f;
-              } else {
-                float Tn[8];
+          const int e = cell, tl = e + 1, l = l0 - K + e;
+          const bool need = (e > t) && (e < ext - 1 - t);
+          if (__any_sync(0xffffffffu, need)) {
+            const bool live = need && (l >= 0) && (l < L);
+            float cand = kInf;
+            if (live) {
+              float Tq[3];
 #pragma unroll
-                for (int n = 0; n < 8; ++n) {
-                  int ds, dl;
-                  nb_tile_offset(dir, n, ds, dl);
-                  Tn[n] = (ds < 0) ? nw[t * P + tl + dl] : old[(t + 1 + ds) * P + tl + dl];
-                }
-                const float *fc = fl + t * EP + e;
-                const size_t cs = (size_t)K * EP;
-                const NodeConst nc = node_const(fc[0], fc[cs], fc[2 * cs], fc[3 * cs], fc[4 * cs], a.h, a.eps);
-                tnew = best_candidate(nc, Tn);
-              }
-              if (e >= K && e < K + R) {
-                const bool ch = (a.tol > 0.0f)
-                                    ? ((tnew < kInf) != (told < kInf)) || fabsf(tnew - told) > a.tol
-                                    : (__float_as_uint(tnew) != __float_as_uint(told));
-                local_changed |= ch;
-              }
+              for (int u = 0; u < 3; ++u)
+                Tq[u] = (nds[u] < 0) ? nw[t * P + tl + ndl[u]] : old[(t + 1 + nds[u]) * P + tl + ndl[u]];
+              const float *tc = tb + t * EP + e;
+              const float len0 = tc[offL0], len1 = tc[offL1], len2 = tc[offL2];
+              const float w0 = sg0 * tc[offW0], w1 = sg1 * tc[offW1], w2 = sg2 * tc[offW2];
+              const float lx = tc[offLx], aa = lx * lx, inv = tc[offInv], det = tc[offDet];
+              float l1, l2;
+              cand = two_point_core(len0, len1, w0, w1, aa, inv, det, Tq[0], Tq[1], l1, l2);
+              cand = fminf(cand, two_point_core(len1, len2, w1, w2, aa, inv, det, Tq[1], Tq[2], l1, l2));
+              cand = fminf(cand, one_point_core(len0, w0, Tq[0]));
+              cand = fminf(cand, one_point_core(len1, w1, Tq[1]));
             }
-            nw[(t + 1) * P + tl] = tnew;
+            cand = fminf(cand, __shfl_xor_sync(0xffffffffu, cand, 1));
+            cand = fminf(cand, __shfl_xor_sync(0xffffffffu, cand, 2));
+            if (q == 0 && need) {
+              float tnew = kInf;
+              if (live) {
+                const float told = old[(t + 1) * P + tl];
+                tnew = sm[t * EP + e] ? 0.0f : cand;
+                if (e >= K && e < K + R) {
+                  const bool ch = (a.tol > 0.0f) ? ((tnew < kInf) != (told < kInf)) || fabsf(tnew - told) > a.tol
+                                                 : (__float_as_uint(tnew) != __float_as_uint(told));
+                  local_changed |= ch;
+                }
+              }
+              nw[(t + 1) * P + tl] = tnew;
+            }
           }
           __syncthreads();
         }
-        // 4. publish the inner lines of this block
-        for (int f = tid; f < K * R; f += nth) {
-          int t, e;
-          if (col) { e = f / K; t = f - e * K; }
-          else     { t = f / R; e = f - t * R; }
-          const int s = s0 + t, l = l0 + e;
-          if (s < S && l < L) nxt[gidx(dir, s, l, a.ny, a.nx)] = nw[(t + 1) * P + K + 1 + e];
+        // 5. publish the inner lines, prefetch the next block, then release
+        const int nwarps = nth >> 5, warp = tid >> 5, lane = tid & 31;
+        if (col) {
+          for (int e = warp; e < R; e += nwarps) {
+            const int l = l0 + e;
+            for (int t = lane; t < K; t += 32) {
+              const int s = s0 + t;
+              if (s < S && l < L) nxt[gidx(dir, s, l, a.ny, a.nx)] = nw[(t + 1) * P + K + 1 + e];
+            }
+          }
+        } else {
+          for (int t = warp; t < K; t += nwarps) {
+            const int s = s0 + t;
+            for (int e = lane; e < R; e += 32) {
+              const int l = l0 + e;
+              if (s < S && l < L) nxt[gidx(dir, s, l, a.ny, a.nx)] = nw[(t + 1) * P + K + 1 + e];
+            }
+          }
         }
+        if (kb + 1 < nblk) prefetch(s0 + K);
         __syncthreads();
         if (tid == 0) {
           __threadfence();
@@ -292,9 +371,12 @@ __global__ void __launch_bounds__(256) record_kernel(RecordArgs a) {
       }
       const float l11 = a.f[p], l21 = a.f[n + p], l22 = a.f[2 * n + p], wx = a.f[3 * n + p],
                   wy = a.f[4 * n + p];
-      const NodeConst nc = node_const(l11, l21, l22, wx, wy, a.h, a.eps);
-      const Winner w = winner(nc, Tn);
-      if (w.value < kInf) r = T0 - w.value;
+      float tab[kTabSize];
+      node_tab(l11, l21, l22, wx, wy, a.h, a.eps, tab);
+      const Winner wall = winner(tab, Tn);
+      if (wall.value < kInf) r = T0 - wall.value;
+      // the record names only donors strictly earlier than the node
+      const Winner w = RECORD ? winner(tab, Tn, T0) : wall;
       if (RECORD && w.id) {
         id = w.id;
         float vx, vy;
@@ -358,36 +440,33 @@ struct SweepPlan {
 
 rf_status plan_sweep(rf_ctx *ctx, int ny, int nx, const rf_opts *o, SweepPlan *pl) {
   int K = (o && o->block > 0) ? o->block : 32;
-  int R = (o && o->band > 0) ? o->band : 64;
-  if (K > R) K = R;
+  int R = (o && o->band > 0) ? o->band : 32;
+  // round the requested shape to one the kernel accepts
+  int k2 = 4;
+  while (k2 * 2 <= K && k2 < 32) k2 *= 2;
+  K = k2;
+  if (R < K) R = K;
+  while (R + 2 * K > kMaxExt && K > 4) K /= 2;
+  if (R + 2 * K > kMaxExt) R = kMaxExt - 2 * K;
+  if (!sweep_shape_ok(R, K)) return RF_ERR_UNSUPPORTED;
   const int maxL = std::max(ny, nx);
   int dev_max_smem = 0;
   cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-  for (int attempt = 0; attempt < 8; ++attempt) {
-    const int ext = R + 2 * K;
-    const int threads = ((ext + 31) / 32) * 32;
-    const size_t smem = sweep_smem_bytes(R, K);
-    if (threads > 1024 || (long long)smem > dev_max_smem) {
-      // shrink the block length first, then give up
-      if (K > 8) { K /= 2; continue; }
-      return RF_ERR_UNSUPPORTED;
-    }
-    cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, threads, smem) != cudaSuccess)
-      return RF_ERR_CUDA;
-    const int grid = (maxL + R - 1) / R;
-    if (per_sm > 0 && grid <= per_sm * ctx->num_sms) {
-      pl->R = R;
-      pl->K = K;
-      pl->grid = grid;
-      pl->threads = threads;
-      pl->smem = smem;
-      return RF_OK;
-    }
-    R *= 2;  // too many bands to be co-resident: widen them
-  }
-  return RF_ERR_UNSUPPORTED;
+  const int threads = sweep_threads(R, K);
+  const size_t smem = sweep_smem_bytes(R, K);
+  if ((long long)smem > dev_max_smem) return RF_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, threads, smem) != cudaSuccess)
+    return RF_ERR_CUDA;
+  const int grid = (maxL + R - 1) / R;
+  if (per_sm < 1 || grid > per_sm * ctx->num_sms) return RF_ERR_UNSUPPORTED;
+  pl->R = R;
+  pl->K = K;
+  pl->grid = grid;
+  pl->threads = threads;
+  pl->smem = smem;
+  return RF_OK;
 }
 
 }  // namespace

@@ -97,4 +97,26 @@ __device__ __forceinline__ void nb_tile_offset(int dir, int n, int &ds, int &dl)
   }
 }
 
+// Copy `total` elements, element f read by ld(f) and written by st(f, v),
+// with B independent loads in flight per thread before the first store, so
+// a block-wide tile fill costs a few memory latencies instead of one per
+// element.
+template <int B, class V, class Ld, class St>
+__device__ __forceinline__ void batched_copy(int total, Ld ld, St st) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int base = tid; base < total; base += B * nth) {
+    V v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int f = base + u * nth;
+      v[u] = (f < total) ? ld(f) : V(0);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int f = base + u * nth;
+      if (f < total) st(f, v[u]);
+    }
+  }
+}
+
 }  // namespace rf

@@ -83,7 +83,26 @@ def test_gradient_parity(case):
     assert e_proj < GRAD_TOL and e_raw < GRAD_TOL, (name, e_lam, e_proj, e_raw, flips.sum())
 
 
-def test_adjoint_kernel_on_oracle_record():
+def test_ordered_adjoint_matches_sweep_and_oracle(case):
+    """RF_ADJ_ORDERED (radix sort on T + dependency-ordered gather) on the
+    GPU record: same lambda as the transposed-sweep adjoint up to float32
+    summation order, and within the gradient tolerance of the oracle."""
+    name, c, gpu, orc = case
+    src = to_dev(c["src"], torch.uint8)
+    T = to_dev(gpu["T"], torch.float32)
+    g = to_dev(c["g"], torch.float32)
+    gproj, lam = api.rf_adjoint(src, T, gpu["rec"], g, algo="ordered")
+    st = api.Context.get(0).stats()
+    assert st["status"] == 0, st
+    lam, gproj = lam.cpu().numpy(), gproj.cpu().numpy()
+    assert rel_l2(lam, gpu["lam"]) < 1e-5
+    assert rel_l2(gproj, gpu["gproj"]) < 1e-5
+    flips, _ = flip_mask(gpu, orc)
+    assert rel_l2(gproj, orc["gproj"], ~flips) < GRAD_TOL
+
+
+@pytest.mark.parametrize("algo", ["sweep", "ordered"])
+def test_adjoint_kernel_on_oracle_record(algo):
     """The adjoint kernel alone, fed the oracle's record (cast to float32):
     lambda and the contracted gradients must match the FP64 back-substitution
     to float32 accuracy."""
@@ -94,7 +113,7 @@ def test_adjoint_kernel_on_oracle_record():
     T = to_dev(orc["T"], torch.float32)
     src = to_dev(c["src"], torch.uint8)
     g = to_dev(np.where(np.isfinite(orc["T"]), c["g"], 0.0), torch.float32)
-    gproj, lam = api.rf_adjoint(src, T, rec, g)
+    gproj, lam = api.rf_adjoint(src, T, rec, g, algo=algo)
     st = api.Context.get(0).stats()
     assert st["status"] == 0
     assert rel_l2(lam.cpu().numpy(), orc["lam"]) < 1e-5
@@ -167,9 +186,17 @@ def test_timeout_path_returns_cleanly():
     st = ctx.stats()
     assert st["status"] == 4  # RF_ERR_TIMEOUT
     ctx.set_timeout(2_000_000_000)
-    T, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], record=False, ctx=ctx)
+    T, rec = api.rf_sweep_forward(proj, c["eps"], src, c["h"], ctx=ctx)
     st = ctx.stats()
     assert st["status"] == 0 and st["converged"]
+    g = to_dev(c["g"], torch.float32)
+    for algo in ("sweep", "ordered"):
+        ctx.set_timeout(0)
+        api.rf_adjoint(src, T, rec, g, algo=algo, ctx=ctx)
+        assert ctx.stats()["status"] == 4, algo  # RF_ERR_TIMEOUT
+        ctx.set_timeout(2_000_000_000)
+        api.rf_adjoint(src, T, rec, g, algo=algo, ctx=ctx)
+        assert ctx.stats()["status"] == 0, algo
 
 
 @pytest.mark.parametrize("band,block", [(32, 8), (64, 32), (128, 16), (16, 16)])
