@@ -214,6 +214,38 @@ rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src,
                      const float *T, const rf_record *rec, const float *dLdT,
                      float *dLdproj5, float *lambda, int algo, void *stream);
 
+/* ---- a10: batched solve ---------------------------------------------------
+ * Many grids of uneven size and source count, forward (+ record, + adjoint
+ * and parameter gradients when dLdT != NULL) in ONE persistent launch.
+ * Paper: batched solves across problem instances (Sec. 3.4 "Computational
+ * Efficiency"); each grid is the discrete system of rf_sweep_forward and
+ * rf_adjoint.
+ * Packed layout: every per-node array holds all grids back to back; grid g
+ * occupies nodes [descs[g].offset, descs[g].offset + ny*nx) of each plane
+ * (row-major inside the grid), and 5-plane arrays have plane stride
+ * total_nodes.  descs: DEVICE array of n_grids descriptors; grids are taken
+ * in array order by the CTAs, so put the largest first.  max_line >= every
+ * grid's max(ny, nx), <= 1024 (sizes the shared memory).  T, rec: outputs
+ * (rec required; the adjoint reads it).  dLdT (nullable) and dLdproj5:
+ * packed like T and proj5.  grid_status (DEVICE, nullable): 3 int32 per grid
+ * = status, forward sweeps, adjoint sweeps.  The call allocates only on
+ * first use (lambda workspace); after one call of the same total size it is
+ * safe to capture in a CUDA graph.  Device errors also go to the context's
+ * status word. */
+typedef struct rf_batch_desc {
+  int32_t ny, nx; /* grid shape */
+  float h;        /* spacing */
+  int32_t pad;
+  int64_t offset; /* first node of the grid in the packed arrays */
+} rf_batch_desc;
+
+rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids,
+                         int64_t total_nodes, int32_t max_line,
+                         const float *proj5, float eps, const uint8_t *src,
+                         const rf_opts *opts, float *T, rf_record *rec,
+                         const float *dLdT, float *dLdproj5,
+                         int32_t *grid_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,11 @@ class Record(ctypes.Structure):
     _fields_ = [("id", ctypes.c_void_p), ("w1", ctypes.c_void_p), ("dT", ctypes.c_void_p)]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("h", ctypes.c_float), ("pad", ctypes.c_int32),
+                ("offset", ctypes.c_int64)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("adj_sweeps", ctypes.c_int32), ("cell_updates", ctypes.c_int64),
@@ -78,6 +83,10 @@ def load(path: str = LIB_PATH):
         "rf_residual": [P, ctypes.POINTER(Grid), P, F, P, P, P, P, P],
         "rf_record_stencils": [P, ctypes.POINTER(Grid), P, F, P, P, ctypes.POINTER(Record), P],
         "rf_adjoint": [P, ctypes.POINTER(Grid), P, P, ctypes.POINTER(Record), P, P, P, I, P],
+        "rf_batch_solve": [P, P, I, ctypes.c_int64, ctypes.c_int32, P, F, P, ctypes.POINTER(Opts), P,
+                           ctypes.POINTER(Record), P, P, P, P],
+        "rf_sweep_forward_static": [ctypes.POINTER(Grid), P, F, P, ctypes.POINTER(Opts), P,
+                                    ctypes.POINTER(Stats), P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

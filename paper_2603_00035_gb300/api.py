@@ -187,3 +187,128 @@ def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=Non
     L.check(L.load().rf_adjoint(ctx.handle, ctypes.byref(g), _ptr(src), _ptr(T), ctypes.byref(crec),
                                 _ptr(dLdT), _ptr(dLdproj5), _ptr(lam_t), int(a), _stream(stream)), "rf_adjoint")
     return dLdproj5, lam_t
+
+
+# ---- a10: batched solve ------------------------------------------------------
+
+BATCH_DESC_DTYPE = None  # numpy structured dtype matching rf_batch_desc
+
+
+def _desc_dtype():
+    import numpy as np
+    global BATCH_DESC_DTYPE
+    if BATCH_DESC_DTYPE is None:
+        BATCH_DESC_DTYPE = np.dtype([("ny", "<i4"), ("nx", "<i4"), ("h", "<f4"), ("pad", "<i4"), ("offset", "<i8")])
+        assert BATCH_DESC_DTYPE.itemsize == ctypes.sizeof(L.BatchDesc)
+    return BATCH_DESC_DTYPE
+
+
+class BatchSolver:
+    """Packs many grids into the layout rf_batch_solve expects and runs the
+    forward (+ adjoint) of all of them in one persistent launch; optionally
+    captured once in a CUDA graph and replayed.
+
+    grids: list of dicts with raw (5, ny, nx) float32, src (ny, nx) uint8,
+    h, and optionally g (ny, nx) float32 (dL/dT).  Grids are stored largest
+    first; `order[k]` is the caller's index of packed grid k.
+    """
+
+    def __init__(self, grids, eps=1e-6, delta=0.05, device="cuda", opts=None, ctx=None):
+        import numpy as np
+        dev = torch.device(device)
+        self.eps, self.delta = float(eps), float(delta)
+        self.ctx = ctx or Context.get(dev)
+        self.opts = opts if opts is not None else make_opts()
+        sizes = [g["src"].size for g in grids]
+        self.order = sorted(range(len(grids)), key=lambda k: -sizes[k])
+        self.n = len(grids)
+        offs, off = [], 0
+        for k in self.order:
+            offs.append(off)
+            off += int(grids[k]["src"].size)
+        self.total = off
+        self.max_line = max(max(g["src"].shape) for g in grids)
+        desc = np.zeros(self.n, dtype=_desc_dtype())
+        raw = np.zeros((5, self.total), np.float32)
+        src = np.zeros(self.total, np.uint8)
+        has_g = all("g" in g for g in grids)
+        gg = np.zeros(self.total, np.float32) if has_g else None
+        for slot, k in enumerate(self.order):
+            g = grids[k]
+            ny, nx = g["src"].shape
+            o = offs[slot]
+            desc[slot] = (ny, nx, g["h"], 0, o)
+            raw[:, o:o + ny * nx] = g["raw"].reshape(5, -1)
+            src[o:o + ny * nx] = g["src"].reshape(-1)
+            if has_g:
+                gg[o:o + ny * nx] = g["g"].reshape(-1)
+        self.offsets = offs
+        self.shapes = [grids[k]["src"].shape for k in self.order]
+        self.desc = torch.from_numpy(desc.view(np.uint8)).to(dev)
+        self.raw = torch.from_numpy(raw).to(dev)
+        self.src = torch.from_numpy(src).to(dev)
+        self.g = torch.from_numpy(gg).to(dev) if has_g else None
+        self.proj = torch.empty_like(self.raw)
+        self.clip = torch.empty(self.total, dtype=torch.uint8, device=dev)
+        self.T = torch.empty(self.total, dtype=torch.float32, device=dev)
+        self.rec = Record(torch.empty(self.total, dtype=torch.uint8, device=dev),
+                          torch.empty(self.total, dtype=torch.float32, device=dev),
+                          torch.empty((5, self.total), dtype=torch.float32, device=dev))
+        self.gproj = torch.empty_like(self.raw) if has_g else None
+        self.graw = torch.empty_like(self.raw) if has_g else None
+        self.gstat = torch.zeros((self.n, 3), dtype=torch.int32, device=dev)
+        self.graph = None
+
+    def _launch(self, stream=None):
+        flat = L.Grid(1, int(self.total), 1.0)
+        lib = L.load()
+        st = _stream(stream)
+        L.check(lib.rf_project(self.ctx.handle, ctypes.byref(flat), _ptr(self.raw), self.eps, self.delta,
+                               _ptr(self.proj), _ptr(self.clip), st), "rf_project")
+        crec = self.rec.c()
+        L.check(lib.rf_batch_solve(self.ctx.handle, _ptr(self.desc), int(self.n), int(self.total),
+                                   int(self.max_line), _ptr(self.proj), self.eps, _ptr(self.src),
+                                   ctypes.byref(self.opts), _ptr(self.T), ctypes.byref(crec), _ptr(self.g),
+                                   _ptr(self.gproj), _ptr(self.gstat), st), "rf_batch_solve")
+        if self.g is not None:
+            L.check(lib.rf_project_backward(self.ctx.handle, ctypes.byref(flat), _ptr(self.raw), _ptr(self.clip),
+                                            self.eps, self.delta, _ptr(self.gproj), _ptr(self.graw), st),
+                    "rf_project_backward")
+
+    def run(self):
+        """Project, solve every grid (and its adjoint), project backward."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._launch()
+
+    def capture(self):
+        """Capture one run in a CUDA graph (after a warm-up run that sizes
+        the workspace); later run() calls replay it."""
+        self._launch()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self._launch(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def grid(self, k, what="T"):
+        """Result of the caller's grid k: T (ny, nx), graw (5, ny, nx) or the
+        record fields."""
+        slot = self.order.index(k)
+        o = self.offsets[slot]
+        ny, nx = self.shapes[slot]
+        if what == "T":
+            return self.T[o:o + ny * nx].view(ny, nx)
+        if what == "graw":
+            return self.graw[:, o:o + ny * nx].reshape(5, ny, nx)
+        if what == "id":
+            return self.rec.id[o:o + ny * nx].view(ny, nx)
+        if what == "status":
+            return self.gstat[slot]
+        raise ValueError(what)

@@ -48,15 +48,6 @@ __host__ __device__ inline size_t adj_smem_bytes(int R, int K) {
   return fl * sizeof(float) + (size_t)(K + 2) * P;
 }
 
-// Weight with which child q (record id, w1) passes lambda to the neighbour in
-// direction `back` (the direction from q to that neighbour); 0 if none.
-__device__ __forceinline__ float child_weight(uint8_t id, float w1, int back) {
-  const int k = id & 7;
-  if (id & 0x10) return (k == back) ? 1.0f : 0.0f;
-  if (id & 0x20) return (k == back) ? w1 : ((((k + 1) & 7) == back) ? 1.0f - w1 : 0.0f);
-  return 0.0f;
-}
-
 constexpr int kAdjLanes = 4;  // lanes per node: lane q gathers neighbours 2q, 2q+1
 
 __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {

@@ -1,0 +1,407 @@
+// rf_batch.cu -- a10: many grids of uneven size and source count solved
+// forward + record + adjoint in one persistent launch.
+//
+// Paper: the batched solves of Sec. 3.4 ("batched approach proves
+// essential"), with the same discrete system as rf_sweep_forward / rf_adjoint
+// (Sec. 3.2, Alg. 1; Sec. 3.3, Alg. 2).
+//
+// GB300 mapping.  CTAs take whole grids from an atomic work counter (the
+// caller orders the descriptors largest first, so long solves start early).
+// A CTA owns its grid alone, so there are no waits between CTAs at all, and
+// its SM's L1 sees every write to the grid (T and lambda are updated in
+// place).  A sweep keeps three lines in shared memory -- this sweep's step
+// s-1 and the pre-sweep steps s, s+1 -- and prefetches step s+2 and the
+// fields of step s+1 into registers while step s is computed; each thread
+// owns up to kBCells nodes of the front.  After the forward converges the
+// CTA records the stencils of its grid and, when dL/dT is given, runs the
+// transposed sweeps for lambda with the same rolling lines, then writes the
+// parameter gradients.
+#include <algorithm>
+
+#include "rf_ctx.h"
+#include "rf_sweep_common.cuh"
+
+namespace rf {
+
+constexpr int kBThreads = 256;
+constexpr int kBCells = 4;  // front nodes per thread: lines up to 1024
+
+struct BatchArgs {
+  const rf_batch_desc *descs;
+  int n_grids;
+  long long total;  // plane stride of the packed arrays
+  int max_line;
+  const float *f;  // 5 planes
+  float eps;
+  const uint8_t *src;
+  float *T;
+  uint8_t *id;
+  float *w1;
+  float *dT;  // 5 planes
+  const float *g;  // nullable: no adjoint
+  float *lam;      // lambda (in place), workspace
+  float *grad;     // 5 planes
+  int max_sweeps, max_adj_sweeps, warm;
+  float tol;
+  int *gstat;  // nullable: [3 * n_grids] status, sweeps, adjoint sweeps
+  unsigned *counter;
+  DevState *st;
+};
+
+__host__ __device__ inline size_t batch_smem_bytes(int max_line) {
+  const size_t W = (size_t)max_line + 2;
+  return 5 * W * sizeof(float) + 4 * W * sizeof(float) + 4 * W;
+}
+
+__global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs a) {
+  extern __shared__ float smem[];
+  const int W = a.max_line + 2;
+  float *rows[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) rows[r] = smem + (size_t)r * W;
+  float *wrow[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) wrow[r] = smem + (size_t)(5 + r) * W;
+  uint8_t *irow[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) irow[r] = (uint8_t *)(smem + (size_t)9 * W) + (size_t)r * W;
+  __shared__ int s_grid;
+  const int tid = threadIdx.x, nth = blockDim.x;
+
+  while (true) {
+    if (tid == 0) s_grid = (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int gi = s_grid;
+    __syncthreads();
+    if (gi >= a.n_grids) break;
+    const rf_batch_desc d = a.descs[gi];
+    const int ny = d.ny, nx = d.nx;
+    const long long n = (long long)ny * nx;
+    const float h = d.h;
+    if (ny < 1 || nx < 1 || ny > a.max_line || nx > a.max_line || !(h > 0.0f)) {
+      if (tid == 0 && a.gstat) a.gstat[3 * gi] = RF_ERR_INVALID_ARG;
+      continue;
+    }
+    float *Tg = a.T + d.offset;
+    const float *fg = a.f + d.offset;
+    const uint8_t *sg = a.src + d.offset;
+
+    // ---- init (a2) -------------------------------------------------------
+    int any_src = 0;
+    for (long long p = tid; p < n; p += nth) {
+      const bool s = sg[p] != 0;
+      any_src |= s;
+      if (s) Tg[p] = 0.0f;
+      else if (!a.warm) Tg[p] = kInf;
+    }
+    any_src = __syncthreads_or(any_src);
+
+    // ---- forward line sweeps (a3, a4) --------------------------------------
+    int sweep = 0, converged = 0;
+    while (any_src) {
+      const int dir = sweep & 3;
+      const bool col = (dir & 1) == 0;
+      const int S = col ? nx : ny, L = col ? ny : nx;
+      float *P = rows[0], *C = rows[1], *N = rows[2], *O = rows[3], *X = rows[4];
+      for (int l = tid; l < W; l += nth) {
+        const int gl = l - 1;
+        const bool in = gl >= 0 && gl < L;
+        P[l] = kInf;
+        O[l] = kInf;
+        X[l] = kInf;
+        C[l] = in ? Tg[gidx(dir, 0, gl, ny, nx)] : kInf;
+        N[l] = (in && S > 1) ? Tg[gidx(dir, 1, gl, ny, nx)] : kInf;
+      }
+      float fv[kBCells][5];
+      uint8_t sv[kBCells];
+#pragma unroll
+      for (int k = 0; k < kBCells; ++k) {
+        const int l = tid + k * nth;
+        const bool ok = l < L;
+        const long long gp = ok ? gidx(dir, 0, l, ny, nx) : 0;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fv[k][c] = ok ? fg[c * a.total + gp] : 1.0f;
+        sv[k] = ok ? sg[gp] : 0;
+      }
+      __syncthreads();
+      int changed = 0;
+      for (int s = 0; s < S; ++s) {
+        // prefetch step s+1's fields and the pre-sweep values of step s+2
+        float fn[kBCells][5], xo[kBCells];
+        uint8_t sn[kBCells];
+#pragma unroll
+        for (int k = 0; k < kBCells; ++k) {
+          const int l = tid + k * nth;
+          const bool ok1 = l < L && s + 1 < S;
+          const long long g1 = ok1 ? gidx(dir, s + 1, l, ny, nx) : 0;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) fn[k][c] = ok1 ? fg[c * a.total + g1] : 1.0f;
+          sn[k] = ok1 ? sg[g1] : 0;
+          const bool ok2 = l < L && s + 2 < S;
+          xo[k] = ok2 ? Tg[gidx(dir, s + 2, l, ny, nx)] : kInf;
+        }
+        // step s: every node of the line from P (step s-1, this sweep),
+        // C (step s) and N (step s+1), both as before the sweep
+#pragma unroll
+        for (int k = 0; k < kBCells; ++k) {
+          const int l = tid + k * nth;
+          if (l < L) {
+            const float told = C[l + 1];
+            float tnew;
+            if (sv[k]) {
+              tnew = 0.0f;
+            } else {
+              float Tn[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                int ds, dl;
+                nb_tile_offset(dir, q, ds, dl);
+                const float *row = ds < 0 ? P : (ds == 0 ? C : N);
+                Tn[q] = row[l + 1 + dl];
+              }
+              float tab[kTabSize];
+              node_tab(fv[k][0], fv[k][1], fv[k][2], fv[k][3], fv[k][4], h, a.eps, tab);
+              tnew = winner(tab, Tn).value;
+            }
+            O[l + 1] = tnew;
+            changed |= (a.tol > 0.0f) ? (((tnew < kInf) != (told < kInf)) || fabsf(tnew - told) > a.tol)
+                                      : (__float_as_uint(tnew) != __float_as_uint(told));
+            Tg[gidx(dir, s, l, ny, nx)] = tnew;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kBCells; ++k) {
+          const int l = tid + k * nth;
+          if (l < L) X[l + 1] = xo[k];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) fv[k][c] = fn[k][c];
+          sv[k] = sn[k];
+        }
+        __syncthreads();
+        // (P, C, N, O, X) <- (O, N, X, P, C)
+        float *t0 = P, *t1 = C;
+        P = O;
+        C = N;
+        N = X;
+        O = t0;
+        X = t1;
+      }
+      changed = __syncthreads_or(changed);
+      ++sweep;
+      if (!changed) {
+        converged = 1;
+        break;
+      }
+      if (sweep >= a.max_sweeps) break;
+    }
+
+    // ---- record (a5) --------------------------------------------------------
+    for (long long p = tid; p < n; p += nth) {
+      const int i = (int)(p / nx), j = (int)(p - (long long)i * nx);
+      uint8_t id;
+      float w1, dd[5], r;
+      record_node(fg, a.total, p, i, j, ny, nx, h, a.eps, sg[p] != 0, Tg, true, id, w1, dd, r);
+      a.id[d.offset + p] = id;
+      a.w1[d.offset + p] = w1;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) a.dT[c * a.total + d.offset + p] = dd[c];
+    }
+    __syncthreads();
+
+    // ---- adjoint (a7, a8): transposed line sweeps, in place -------------------
+    int asweep = 0, aconv = 1;
+    if (a.g) {
+      float *Lg = a.lam + d.offset;
+      const uint8_t *ig = a.id + d.offset;
+      const float *wg = a.w1 + d.offset;
+      const float *gg = a.g + d.offset;
+      for (long long p = tid; p < n; p += nth) Lg[p] = 0.0f;
+      __syncthreads();
+      aconv = 0;
+      while (true) {
+        const int dir = asweep & 3;
+        const bool col = (dir & 1) == 0;
+        const int S = col ? nx : ny, L = col ? ny : nx;
+        float *P = rows[0], *C = rows[1], *N = rows[2], *O = rows[3], *X = rows[4];
+        float *WP = wrow[0], *WC = wrow[1], *WN = wrow[2], *WX = wrow[3];
+        uint8_t *IP = irow[0], *IC = irow[1], *IN = irow[2], *IX = irow[3];
+        for (int l = tid; l < W; l += nth) {
+          const int gl = l - 1;
+          const bool in = gl >= 0 && gl < L;
+          P[l] = 0.0f;
+          O[l] = 0.0f;
+          X[l] = 0.0f;
+          WP[l] = 0.0f;
+          IP[l] = 0;
+          WX[l] = 0.0f;
+          IX[l] = 0;
+          const long long g0 = in ? gidx(dir, 0, gl, ny, nx) : 0;
+          const long long g1 = (in && S > 1) ? gidx(dir, 1, gl, ny, nx) : 0;
+          C[l] = in ? Lg[g0] : 0.0f;
+          WC[l] = in ? wg[g0] : 0.0f;
+          IC[l] = in ? ig[g0] : 0;
+          N[l] = (in && S > 1) ? Lg[g1] : 0.0f;
+          WN[l] = (in && S > 1) ? wg[g1] : 0.0f;
+          IN[l] = (in && S > 1) ? ig[g1] : 0;
+        }
+        float gv[kBCells];
+#pragma unroll
+        for (int k = 0; k < kBCells; ++k) {
+          const int l = tid + k * nth;
+          const long long gp = l < L ? gidx(dir, 0, l, ny, nx) : 0;
+          gv[k] = (l < L && Tg[gp] < kInf) ? gg[gp] : 0.0f;
+        }
+        __syncthreads();
+        int changed = 0;
+        for (int s = 0; s < S; ++s) {
+          float gn[kBCells], xl[kBCells], xw[kBCells];
+          uint8_t xi[kBCells];
+#pragma unroll
+          for (int k = 0; k < kBCells; ++k) {
+            const int l = tid + k * nth;
+            const bool ok1 = l < L && s + 1 < S;
+            const long long g1 = ok1 ? gidx(dir, s + 1, l, ny, nx) : 0;
+            gn[k] = (ok1 && Tg[g1] < kInf) ? gg[g1] : 0.0f;
+            const bool ok2 = l < L && s + 2 < S;
+            const long long g2 = ok2 ? gidx(dir, s + 2, l, ny, nx) : 0;
+            xl[k] = ok2 ? Lg[g2] : 0.0f;
+            xw[k] = ok2 ? wg[g2] : 0.0f;
+            xi[k] = ok2 ? ig[g2] : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < kBCells; ++k) {
+            const int l = tid + k * nth;
+            if (l < L) {
+              const float lold = C[l + 1];
+              float acc = gv[k];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                int ds, dl;
+                nb_tile_offset(dir, q, ds, dl);
+                const int c = l + 1 + dl;
+                const float wq = child_weight(ds < 0 ? IP[c] : (ds == 0 ? IC[c] : IN[c]),
+                                              ds < 0 ? WP[c] : (ds == 0 ? WC[c] : WN[c]), (q + 4) & 7);
+                if (wq != 0.0f) acc = fmaf(wq, ds < 0 ? P[c] : (ds == 0 ? C[c] : N[c]), acc);
+              }
+              O[l + 1] = acc;
+              changed |= (__float_as_uint(acc) != __float_as_uint(lold));
+              Lg[gidx(dir, s, l, ny, nx)] = acc;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < kBCells; ++k) {
+            const int l = tid + k * nth;
+            if (l < L) {
+              X[l + 1] = xl[k];
+              WX[l + 1] = xw[k];
+              IX[l + 1] = xi[k];
+            }
+            gv[k] = gn[k];
+          }
+          __syncthreads();
+          float *t0 = P, *t1 = C;
+          P = O;
+          C = N;
+          N = X;
+          O = t0;
+          X = t1;
+          float *u0 = WP;
+          WP = WC;
+          WC = WN;
+          WN = WX;
+          WX = u0;
+          uint8_t *v0 = IP;
+          IP = IC;
+          IC = IN;
+          IN = IX;
+          IX = v0;
+        }
+        changed = __syncthreads_or(changed);
+        ++asweep;
+        if (!changed) {
+          aconv = 1;
+          break;
+        }
+        if (asweep >= a.max_adj_sweeps) break;
+      }
+      // a8: parameter gradients
+      for (long long p = tid; p < n; p += nth) {
+        const bool act = ig[p] != 0 && !sg[p];
+        const float lam = Lg[p];
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          a.grad[c * a.total + d.offset + p] = act ? lam * a.dT[c * a.total + d.offset + p] : 0.0f;
+      }
+    }
+    if (tid == 0) {
+      const int stc = !any_src ? RF_ERR_NO_SOURCE : (!converged || !aconv) ? RF_ERR_NOT_CONVERGED : RF_OK;
+      if (a.gstat) {
+        a.gstat[3 * gi] = stc;
+        a.gstat[3 * gi + 1] = sweep;
+        a.gstat[3 * gi + 2] = asweep;
+      }
+      if (stc != RF_OK) set_error(a.st, stc);
+      atomicAdd(&a.st->cell_updates, (unsigned long long)sweep * (unsigned long long)n);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace rf
+
+using namespace rf;
+
+extern "C" rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids, int64_t total_nodes,
+                                    int32_t max_line, const float *proj5, float eps, const uint8_t *src,
+                                    const rf_opts *opts, float *T, rf_record *rec, const float *dLdT,
+                                    float *dLdproj5, int32_t *grid_status, void *stream) {
+  if (!ctx || !descs || n_grids < 1 || total_nodes < 1 || !proj5 || !src || !T || !rec || !rec->id || !rec->w1 ||
+      !rec->dT)
+    return RF_ERR_INVALID_ARG;
+  if (max_line < 1 || max_line > kBThreads * kBCells || !(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
+  if (dLdT && !dLdproj5) return RF_ERR_INVALID_ARG;
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0};
+  if (opts) o = *opts;
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+    return RF_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  rf_status rs;
+  if (dLdT && (rs = ensure(&ctx->lbuf, &ctx->lbuf_cap, (size_t)total_nodes)) != RF_OK) return rs;
+  if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)2)) != RF_OK) return rs;
+  const size_t smem = batch_smem_bytes(max_line);
+  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RF_ERR_UNSUPPORTED;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    return RF_ERR_UNSUPPORTED;
+  cudaMemsetAsync(ctx->changed, 0, sizeof(int), s);  // work counter
+  cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
+  BatchArgs a;
+  a.descs = descs;
+  a.n_grids = n_grids;
+  a.total = total_nodes;
+  a.max_line = max_line;
+  a.f = proj5;
+  a.eps = eps;
+  a.src = src;
+  a.T = T;
+  a.id = rec->id;
+  a.w1 = rec->w1;
+  a.dT = rec->dT;
+  a.g = dLdT;
+  a.lam = ctx->lbuf;
+  a.grad = dLdproj5;
+  a.max_sweeps = o.max_sweeps;
+  a.max_adj_sweeps = 4 * o.max_sweeps;
+  a.warm = o.mode == RF_MODE_WARM;
+  a.tol = o.tol;
+  a.gstat = grid_status;
+  a.counter = (unsigned *)ctx->changed;
+  a.st = ctx->state;
+  const int grid = std::min(per_sm * ctx->num_sms, n_grids);
+  batch_kernel<<<grid, kBThreads, smem, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}

@@ -347,10 +347,7 @@ struct RecordArgs {
 };
 
 // a5: stencil identification + closed-form partials at the converged T
-// (Alg. 2 first loop; App. A partials).  For the winning update with
-// barycentric weights (w1, 1 - w1) the characteristic displacement is
-// v = w1 m1 + (1-w1) m2 (v = m_n for a one-point update) and
-//   dT0/dw = -v,   dT0/dM = v v^T / (2 |v|_M),   dT0/dL = 2 (dT0/dM) L.
+// (record_node), with the max |residual| reduced per block.
 template <bool RECORD>
 __global__ void __launch_bounds__(256) record_kernel(RecordArgs a) {
   const long long n = (long long)a.ny * a.nx;
@@ -358,52 +355,9 @@ __global__ void __launch_bounds__(256) record_kernel(RecordArgs a) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(p / a.nx), j = (int)(p - (long long)i * a.nx);
-    const float T0 = a.T[p];
-    uint8_t id = 0;
-    float w1 = 0.0f, d[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    float r = 0.0f;
-    if (!a.src[p] && T0 < kInf) {
-      float Tn[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int ii = i + nb_dy(q), jj = j + nb_dx(q);
-        Tn[q] = (ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx) ? a.T[(long long)ii * a.nx + jj] : kInf;
-      }
-      const float l11 = a.f[p], l21 = a.f[n + p], l22 = a.f[2 * n + p], wx = a.f[3 * n + p],
-                  wy = a.f[4 * n + p];
-      float tab[kTabSize];
-      node_tab(l11, l21, l22, wx, wy, a.h, a.eps, tab);
-      const Winner wall = winner(tab, Tn);
-      if (wall.value < kInf) r = T0 - wall.value;
-      // the record names only donors strictly earlier than the node
-      const Winner w = RECORD ? winner(tab, Tn, T0) : wall;
-      if (RECORD && w.id) {
-        id = w.id;
-        float vx, vy;
-        const int k = w.id & 7;
-        if (w.id & 0x20) {
-          const float sum = w.l1 + w.l2;
-          w1 = sum > 0.0f ? w.l1 / sum : 0.5f;
-          const int k2 = (k + 1) & 7;
-          vx = a.h * (w1 * (float)nb_dx(k) + (1.0f - w1) * (float)nb_dx(k2));
-          vy = a.h * (w1 * (float)nb_dy(k) + (1.0f - w1) * (float)nb_dy(k2));
-        } else {
-          w1 = 1.0f;
-          vx = a.h * (float)nb_dx(k);
-          vy = a.h * (float)nb_dy(k);
-        }
-        const float m11 = fmaf(l11, l11, a.eps), m12 = l11 * l21,
-                    m22 = fmaf(l21, l21, fmaf(l22, l22, a.eps));
-        const float vm = sqrtf(vx * (m11 * vx + m12 * vy) + vy * (m12 * vx + m22 * vy));
-        const float s = 0.5f / vm;
-        const float D11 = s * vx * vx, D12 = s * vx * vy, D22 = s * vy * vy;
-        d[0] = 2.0f * (D11 * l11 + D12 * l21);
-        d[1] = 2.0f * (D12 * l11 + D22 * l21);
-        d[2] = 2.0f * D22 * l22;
-        d[3] = -vx;
-        d[4] = -vy;
-      }
-    }
+    uint8_t id;
+    float w1, d[5], r;
+    record_node(a.f, n, p, i, j, a.ny, a.nx, a.h, a.eps, a.src[p] != 0, a.T, RECORD, id, w1, d, r);
     if (RECORD) {
       a.id[p] = id;
       a.w1[p] = w1;

@@ -1,0 +1,103 @@
+"""rf_batch_solve: many grids of uneven size (square and 2:1) and source
+count in one persistent launch, checked against the single-grid CUDA path
+(same discrete system, same sweep schedule) and the FP64 oracle, and
+replayed from a CUDA graph."""
+import numpy as np
+import pytest
+
+import oracle as O
+import rf_inputs as R
+from gpu_util import FWD_TOL, GRAD_TOL, rel_l2, require_gpu, to_dev, torch
+from paper_2603_00035_gb300 import api
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def make_grids(count=10, seed=0, lo=17, hi=150):
+    rng = np.random.default_rng(seed)
+    grids = []
+    for b in range(count):
+        s = int(rng.integers(lo, hi + 1))
+        ny, nx = (s, s) if b % 2 == 0 else (max(2, s // 2), s)
+        h = 1.0 / (max(ny, nx) - 1)
+        raw = R.randers_fields(ny, nx, h, 8, seed=seed * 100 + b, omega="unit", omega_scale=0.3)
+        src = R.random_sources(ny, nx, int(rng.integers(1, 5)), seed=seed * 100 + b)
+        g = R.sparse_loss_grad(ny, nx, 0.05, seed=b)
+        grids.append(dict(raw=raw, src=src, h=h, g=g))
+    return grids
+
+
+@pytest.fixture(scope="module")
+def solved():
+    grids = make_grids()
+    bs = api.BatchSolver(grids)
+    bs.run()
+    torch.cuda.synchronize()
+    return grids, bs
+
+
+def test_batch_matches_single_grid_path(solved):
+    grids, bs = solved
+    assert api.Context.get(0).stats()["status"] == 0
+    for k, g in enumerate(grids):
+        st = bs.grid(k, "status").cpu().numpy()
+        assert st[0] == 0, (k, st)
+        raw = to_dev(g["raw"], torch.float32)
+        src = to_dev(g["src"], torch.uint8)
+        proj, clip = api.rf_project(raw, 1e-6, 0.05)
+        T, rec = api.rf_sweep_forward(proj, 1e-6, src, g["h"])
+        sref = api.Context.get(0).stats()
+        # same schedule; only FMA contraction may differ between the kernels
+        assert abs(int(st[1]) - sref["sweeps"]) <= 2, (k, st, sref)
+        Tb = bs.grid(k, "T")
+        assert (Tb - T).abs().max().item() <= 1e-6 * T.max().item(), k
+        assert (bs.grid(k, "id") == rec.id).float().mean().item() > 0.999, k
+        gproj, _ = api.rf_adjoint(src, T, rec, to_dev(g["g"], torch.float32), algo="ordered")
+        graw = api.rf_project_backward(raw, clip, 1e-6, 0.05, gproj)
+        assert rel_l2(bs.grid(k, "graw").cpu().numpy(), graw.cpu().numpy()) < 1e-5, k
+
+
+def test_batch_matches_oracle(solved):
+    grids, bs = solved
+    for k, g in enumerate(grids[:4]):
+        orc = O.solve_and_grad(g["raw"].astype(np.float64), g["src"], g["h"], 1e-6, 0.05, g["g"].astype(np.float64))
+        Tb = bs.grid(k, "T").cpu().numpy()
+        tmax = orc["T"].max()
+        assert np.abs(Tb - orc["T"]).max() <= FWD_TOL * tmax, k
+        ids = bs.grid(k, "id").cpu().numpy()
+        flips = (ids != orc["rec"]["id"]) | (orc["rec"]["margin"] < 1e-5 * tmax)
+        assert rel_l2(bs.grid(k, "graw").cpu().numpy(), orc["graw"], ~flips) < GRAD_TOL, k
+
+
+def test_batch_graph_replay_reproduces(solved):
+    grids = make_grids(count=6, seed=3)
+    bs = api.BatchSolver(grids)
+    bs.run()
+    torch.cuda.synchronize()
+    T0 = bs.T.clone()
+    G0 = bs.graw.clone()
+    bs.capture()
+    bs.T.fill_(-1.0)
+    bs.graw.fill_(0.0)
+    for _ in range(2):
+        bs.run()
+    torch.cuda.synchronize()
+    assert torch.equal(bs.T, T0)
+    assert torch.equal(bs.graw, G0)
+    assert int(bs.gstat[:, 0].abs().sum()) == 0
+
+
+def test_batch_grid_without_source_is_reported():
+    grids = make_grids(count=3, seed=5)
+    grids[1]["src"] = np.zeros_like(grids[1]["src"])
+    bs = api.BatchSolver(grids)
+    bs.run()
+    torch.cuda.synchronize()
+    assert int(bs.grid(1, "status")[0]) == 6  # RF_ERR_NO_SOURCE
+    assert int(bs.grid(0, "status")[0]) == 0 and int(bs.grid(2, "status")[0]) == 0
+    api.Context.get(0).stats()  # clear the status word
