@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256"],
+                   help="inverse2048: one 2048^2 grid per step (the headline); batch256: 256 grids of sides "
+                        "64..1024 per step through rf_batch_solve, with the plain per-grid form beside it")
+    p.add_argument("--grids", type=int, default=256)
     return p.parse_args()
 
 
@@ -337,10 +341,98 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def batch_grids(count, seed=0):
+    """The batched workload: long side s ~ U{64..1024}, half square, half
+    2:1; fields as the 64x64 workload (8 modes, |w| = 0.3); 1-8 sources;
+    dL/dT on 1 % of the nodes."""
+    import rf_inputs as R
+    rng = np.random.default_rng(seed)
+    grids = []
+    for b, (ny, nx) in enumerate(R.batch_shapes(count, seed)):
+        h = 1.0 / (max(ny, nx) - 1)
+        grids.append(dict(raw=R.randers_fields(ny, nx, h, 8, seed * 1000 + b, omega="unit", omega_scale=0.3),
+                          src=R.random_sources(ny, nx, int(rng.integers(1, 9)), seed * 1000 + b),
+                          g=R.sparse_loss_grad(ny, nx, 0.01, b), h=h))
+    return grids
+
+
+def run_batch(args):
+    import torch
+
+    from paper_2603_00035_gb300 import api
+    from paper_2603_00035_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(0)
+    grids = batch_grids(args.grids)
+    nodes = sum(g["src"].size for g in grids)
+    bs = api.BatchSolver(grids)
+    bs.run()
+    torch.cuda.synchronize()
+    bs.capture()
+    for _ in range(args.warmup):
+        bs.run()
+    torch.cuda.synchronize()
+    st = api.Context.get(0).stats()
+    if st["status"] != 0 or int(bs.gstat[:, 0].abs().sum()) != 0:
+        raise RuntimeError(f"batch status {st}, per-grid {bs.gstat[:, 0].tolist()}")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        bs.run()
+    e1.record()
+    torch.cuda.synchronize()
+    sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    sweeps = bs.gstat[:, 1].double().mean().item()
+    # the plain form: one grid after another through the single-grid entry points
+    dev = torch.device("cuda")
+    per = []
+    for g in grids:
+        raw = torch.from_numpy(g["raw"]).to(dev)
+        src = torch.from_numpy(g["src"]).to(dev)
+        gg = torch.from_numpy(g["g"]).to(dev)
+        per.append((raw, src, gg, g["h"]))
+
+    def plain():
+        for raw, src, gg, h in per:
+            proj, clip = api.rf_project(raw, 1e-6, 0.05)
+            T, rec = api.rf_sweep_forward(proj, 1e-6, src, h)
+            gproj, _ = api.rf_adjoint(src, T, rec, gg, algo="ordered", lam=False)
+            api.rf_project_backward(raw, clip, 1e-6, 0.05, gproj)
+
+    plain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record()
+    plain()
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    line = {"metric": f"forward+adjoint solves/s, batch of {len(grids)} grids (sides 64..1024)",
+            "value": len(grids) / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched forward+adjoint, {len(grids)} grids, long side U{{64..1024}}, "
+                                   "half square / half 2:1, 1-8 sources, one persistent launch in a CUDA graph",
+                       "nodes": int(nodes), "mean_sweeps": sweeps,
+                       "l2": "working set > L2 (%.0f MB of fields)" % (nodes * 20 / 1e6)},
+            "plain_form": {"value": len(grids) / (plain_ms / 1e3), "unit": UNIT, "ms_per_batch": plain_ms,
+                           "how": "rf_project, rf_sweep_forward, rf_adjoint(ordered), rf_project_backward per grid"},
+            "gpu_launches": 3 * args.steps,
+            "clocks": sampler.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch256":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -65,13 +65,18 @@ enum rf_adjoint_algo {
 };
 
 typedef struct rf_opts {
-  float tol;          /* a node counts as changed when |T_new - T_old| > tol;
-                         0 = exact (stop at the first sweep that changes
-                         nothing, which is then a fixed point)              */
+  float tol;          /* absolute part of the change test (see rtol)        */
   int32_t max_sweeps; /* cap on directional sweeps (4 per iteration)       */
   int32_t mode;       /* enum rf_mode                                       */
   int32_t band;       /* lines per band (0 = auto)                          */
   int32_t block;      /* line steps per block, <= band (0 = auto)           */
+  float rtol;         /* a node counts as changed in a sweep when
+                         |T_new - T_old| > tol + rtol * T_new (either value
+                         +inf: changed unless both are); the solve stops at
+                         the first sweep with no changed node.  tol = rtol =
+                         0 asks for bitwise no-change, which FP32 rounding
+                         can turn into an ulp-level 2-cycle; the default
+                         (opts NULL) is tol 0, rtol 1e-6 (about 8 ulp)     */
 } rf_opts;
 
 /* Per-node record of the converged forward solve (Alg. 2, first loop). */
@@ -152,7 +157,7 @@ rf_status rf_project_backward(rf_ctx *ctx, const rf_grid *grid,
  * rec (nullable): when given, the stencil id, donor weight and the partials
  * dT0/dtheta of every node's winning update at the converged T are written
  * (Alg. 2 "Identify active stencil"; App. A closed-form partials), plus the
- * max residual into the stats.  opts may be NULL (defaults: tol 0,
+ * max residual into the stats.  opts may be NULL (defaults: tol 0, rtol 1e-6,
  * max_sweeps 64, cold start, automatic band/block). */
 rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid,
                            const float *proj5, float eps, const uint8_t *src,

@@ -33,7 +33,7 @@ class Grid(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("max_sweeps", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("band", ctypes.c_int32), ("block", ctypes.c_int32)]
+                ("band", ctypes.c_int32), ("block", ctypes.c_int32), ("rtol", ctypes.c_float)]
 
 
 class Record(ctypes.Structure):

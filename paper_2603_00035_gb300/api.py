@@ -122,8 +122,11 @@ def rf_project_backward(raw5, clip, eps, delta, dproj5, draw5=None, ctx=None, st
     return draw5
 
 
-def make_opts(tol=0.0, max_sweeps=64, warm=False, band=0, block=0):
-    return L.Opts(float(tol), int(max_sweeps), L.RF_MODE_WARM if warm else L.RF_MODE_COLD, int(band), int(block))
+def make_opts(tol=0.0, max_sweeps=64, warm=False, band=0, block=0, rtol=1e-6):
+    """rf_opts: a node counts as changed when |dT| > tol + rtol * T (tol =
+    rtol = 0: bitwise); the sweep stops at the first sweep with no change."""
+    return L.Opts(float(tol), int(max_sweeps), L.RF_MODE_WARM if warm else L.RF_MODE_COLD, int(band), int(block),
+                  float(rtol))
 
 
 def rf_sweep_forward(proj5, eps, src, h, opts=None, T=None, record=True, rec=None, ctx=None, stream=None):

@@ -23,8 +23,8 @@
 
 namespace rf {
 
-constexpr int kBThreads = 256;
-constexpr int kBCells = 4;  // front nodes per thread: lines up to 1024
+constexpr int kBThreads = 512;
+constexpr int kBCells = 2;  // front nodes per thread: lines up to 1024
 
 struct BatchArgs {
   const rf_batch_desc *descs;
@@ -42,7 +42,7 @@ struct BatchArgs {
   float *lam;      // lambda (in place), workspace
   float *grad;     // 5 planes
   int max_sweeps, max_adj_sweeps, warm;
-  float tol;
+  float tol, rtol;
   int *gstat;  // nullable: [3 * n_grids] status, sweeps, adjoint sweeps
   unsigned *counter;
   DevState *st;
@@ -53,7 +53,7 @@ __host__ __device__ inline size_t batch_smem_bytes(int max_line) {
   return 5 * W * sizeof(float) + 4 * W * sizeof(float) + 4 * W;
 }
 
-__global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchArgs a) {
   extern __shared__ float smem[];
   const int W = a.max_line + 2;
   float *rows[5];
@@ -164,8 +164,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(BatchArgs a) {
               tnew = winner(tab, Tn).value;
             }
             O[l + 1] = tnew;
-            changed |= (a.tol > 0.0f) ? (((tnew < kInf) != (told < kInf)) || fabsf(tnew - told) > a.tol)
-                                      : (__float_as_uint(tnew) != __float_as_uint(told));
+            changed |= node_changed(tnew, told, a.tol, a.rtol);
             Tg[gidx(dir, s, l, ny, nx)] = tnew;
           }
         }
@@ -360,9 +359,9 @@ extern "C" rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int
     return RF_ERR_INVALID_ARG;
   if (max_line < 1 || max_line > kBThreads * kBCells || !(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
   if (dLdT && !dLdproj5) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f};
   if (opts) o = *opts;
-  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
     return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -398,6 +397,7 @@ extern "C" rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int
   a.max_adj_sweeps = 4 * o.max_sweeps;
   a.warm = o.mode == RF_MODE_WARM;
   a.tol = o.tol;
+  a.rtol = o.rtol;
   a.gstat = grid_status;
   a.counter = (unsigned *)ctx->changed;
   a.st = ctx->state;

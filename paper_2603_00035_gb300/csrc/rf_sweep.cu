@@ -41,7 +41,7 @@ struct SweepArgs {
   float *Tb;  // workspace
   int R, K;
   int max_sweeps;
-  float tol;
+  float tol, rtol;
   unsigned tok_stride;  // progress tokens per sweep
   unsigned *progress;   // [gridDim.x]
   int *changed;         // [max_sweeps]
@@ -245,9 +245,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
                 const float told = old[(t + 1) * P + tl];
                 tnew = sm[t * EP + e] ? 0.0f : cand;
                 if (e >= K && e < K + R) {
-                  const bool ch = (a.tol > 0.0f) ? ((tnew < kInf) != (told < kInf)) || fabsf(tnew - told) > a.tol
-                                                 : (__float_as_uint(tnew) != __float_as_uint(told));
-                  local_changed |= ch;
+                  local_changed |= node_changed(tnew, told, a.tol, a.rtol);
                 }
               }
               nw[(t + 1) * P + tl] = tnew;
@@ -431,9 +429,9 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   if (!ctx || !grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
   if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
   if (rec && (!rec->id || !rec->w1 || !rec->dT)) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f};
   if (opts) o = *opts;
-  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
     return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -475,6 +473,7 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   a.K = pl.K;
   a.max_sweeps = o.max_sweeps;
   a.tol = o.tol;
+  a.rtol = o.rtol;
   a.tok_stride = (unsigned)((std::max(ny, nx) + pl.K - 1) / pl.K + 1);
   a.progress = ctx->progress;
   a.changed = ctx->changed;
@@ -604,9 +603,9 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
                                              rf_stats *stats, void *stream) {
   if (!grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
   if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f};
   if (opts) o = *opts;
-  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
     return RF_ERR_INVALID_ARG;
   const int ny = grid->ny, nx = grid->nx;
   const long long n = (long long)ny * nx;
@@ -667,6 +666,7 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
   a.K = pl.K;
   a.max_sweeps = o.max_sweeps;
   a.tol = o.tol;
+  a.rtol = o.rtol;
   a.tok_stride = (unsigned)((std::max(ny, nx) + pl.K - 1) / pl.K + 1);
   a.progress = progress;
   a.changed = changed;

@@ -97,6 +97,16 @@ __device__ __forceinline__ void nb_tile_offset(int dir, int n, int &ds, int &dl)
   }
 }
 
+// Change test of the forward sweeps: |tnew - told| > tol + rtol * tnew,
+// +inf on exactly one side counts as changed; tol = rtol = 0 is bitwise.
+__device__ __forceinline__ bool node_changed(float tnew, float told, float tol, float rtol) {
+  if (tol == 0.0f && rtol == 0.0f) return __float_as_uint(tnew) != __float_as_uint(told);
+  const bool fn = tnew < kInf, fo = told < kInf;
+  if (fn != fo) return true;
+  if (!fn) return false;
+  return fabsf(tnew - told) > fmaf(rtol, fabsf(tnew), tol);
+}
+
 // Copy `total` elements, element f read by ld(f) and written by st(f, v),
 // with B independent loads in flight per thread before the first store, so
 // a block-wide tile fill costs a few memory latencies instead of one per

@@ -210,3 +210,19 @@ def test_band_and_block_shapes_agree(band, block):
     st = api.Context.get(0).stats()
     assert st["status"] == 0 and st["converged"]
     assert np.abs(T.cpu().numpy() - To).max() <= FWD_TOL * To.max()
+
+
+@pytest.mark.parametrize("which", ["config1", "config2"])
+def test_bitwise_change_test_still_converges_here(which):
+    """tol = rtol = 0 (stop only at a sweep with no bitwise change) proves a
+    fixed point when it terminates; on these workloads it does, and agrees
+    with the default relative test."""
+    c = CASES[which]()
+    proj, _ = api.rf_project(to_dev(c["raw"], torch.float32), c["eps"], c["delta"])
+    src = to_dev(c["src"], torch.uint8)
+    T0, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], opts=api.make_opts(rtol=0.0), record=False)
+    st = api.Context.get(0).stats()
+    assert st["status"] == 0 and st["converged"]
+    T1, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], record=False)
+    assert api.Context.get(0).stats()["status"] == 0
+    assert (T0 - T1).abs().max().item() <= 1e-5 * T0.max().item()
