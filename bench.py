@@ -201,7 +201,14 @@ def run_ours(args):
     src = torch.from_numpy(c["src"]).to(dev)
     g = torch.from_numpy(c["g"]).to(dev)
     ctx = api.Context.get(local)
-    opts = api.make_opts(band=args.band, block=args.block)
+    tile = {"band": args.band, "block": args.block, "autotuned": False}
+    if not (args.band and args.block):
+        from paper_2603_00035_gb300 import autotune
+        proj0, _ = api.rf_project(raw, eps, delta)
+        b_, k_ = autotune.tune_sweep(proj0, eps, src, h)
+        tile = {"band": b_, "block": k_, "autotuned": True, "cache": autotune.cache_path()}
+        del proj0
+    opts = api.make_opts(band=tile["band"], block=tile["block"])
     stream = torch.cuda.current_stream()
     # preallocated outputs: the timed steps allocate nothing
     proj = torch.empty_like(raw)
@@ -321,7 +328,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(n),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": dict(workload_config(n), tile=tile),
             "roofline": roofline, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP[args.algo] * args.steps,
             "clocks": sampler.summary(),
             "solver": {"sweeps": sweeps, "adj_sweeps": adj_sweeps, "cell_updates": cell_updates,

@@ -1,0 +1,121 @@
+"""Autotuner for the line-tile shape of the forward sweep.
+
+rf_sweep_forward splits every sweep's lines into bands of R lines (one CTA
+each) and advances a band K line steps per block (halo of K lines).  The
+best (R, K) depends on the grid size and the GPU.  tune_sweep() times the
+candidate shapes on a real solve and keeps the fastest per grid-size bucket
+(next power of two of max(ny, nx)); results are cached in a JSON file keyed
+by the GPU name, so later processes reuse them without timing again.
+
+Cache file: $RF_AUTOTUNE_CACHE, else ~/.cache/rf_gb300/autotune.json.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+CANDIDATES = [(32, 32), (16, 16), (32, 16), (48, 16), (64, 32), (24, 8)]
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    p = os.environ.get("RF_AUTOTUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "rf_gb300", "autotune.json")
+
+
+def bucket(ny: int, nx: int) -> int:
+    m = max(int(ny), int(nx), 1)
+    b = 1
+    while b < m:
+        b *= 2
+    return b
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict) -> None:
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def lookup(device_name: str, ny: int, nx: int):
+    """(band, block) cached for this GPU and size bucket, or None."""
+    with _lock:
+        e = _load().get(device_name, {}).get(str(bucket(ny, nx)))
+    return (int(e["band"]), int(e["block"])) if e else None
+
+
+def record(device_name: str, ny: int, nx: int, band: int, block: int, ms: float, table=None) -> None:
+    with _lock:
+        d = _load()
+        d.setdefault(device_name, {})[str(bucket(ny, nx))] = {"band": int(band), "block": int(block),
+                                                              "ms": float(ms), "timings": table or {}}
+        _store(d)
+
+
+def choose(timings: dict):
+    """Fastest (band, block) of {(band, block): ms}; ties go to the first."""
+    best = None
+    for shape, ms in timings.items():
+        if best is None or ms < timings[best]:
+            best = shape
+    return best
+
+
+def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
+    """Time rf_sweep_forward for each candidate (band, block) on this input,
+    cache and return the fastest.  Uses the cached result unless force."""
+    import torch
+
+    from . import api
+
+    ny, nx = src.shape
+    name = torch.cuda.get_device_name(proj5.device)
+    if not force:
+        hit = lookup(name, ny, nx)
+        if hit is not None:
+            return hit
+    T = torch.empty((ny, nx), dtype=torch.float32, device=proj5.device)
+    timings = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for band, block in (candidates or CANDIDATES):
+        o = api.make_opts(band=band, block=block)
+        try:
+            api.rf_sweep_forward(proj5, eps, src, h, opts=o, T=T, record=False)
+        except Exception:
+            continue  # shape not supported on this device
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(repeats):
+            api.rf_sweep_forward(proj5, eps, src, h, opts=o, T=T, record=False)
+        e1.record()
+        torch.cuda.synchronize()
+        timings[(band, block)] = e0.elapsed_time(e1) / repeats
+    api.Context.get(proj5.device).stats()
+    best = choose(timings)
+    record(name, ny, nx, best[0], best[1], timings[best], {f"{b}x{k}": round(v, 4) for (b, k), v in timings.items()})
+    return best
+
+
+def best_opts(device_name: str, ny: int, nx: int, **kw):
+    """api.make_opts with the cached shape for this bucket (defaults otherwise)."""
+    from . import api
+    hit = lookup(device_name, ny, nx)
+    if hit is not None:
+        kw.setdefault("band", hit[0])
+        kw.setdefault("block", hit[1])
+    return api.make_opts(**kw)
