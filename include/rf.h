@@ -251,6 +251,95 @@ rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids,
                          const float *dLdT, float *dLdproj5,
                          int32_t *grid_status, void *stream);
 
+/* ---- a11, a12: kernels of the learned warm start ---------------------------
+ * The paper has no network; these serve the build's learned initial guess
+ * (a small U-Net, BF16 weights/activations, FP32 accumulation) that enters
+ * rf_sweep_forward through RF_MODE_WARM.  Tensors are NHWC, BF16 values
+ * passed as uint16_t (IEEE bfloat16 bit patterns); every channel count given
+ * to a convolution is a multiple of 16.  All pointers are device memory
+ * owned by the caller; calls only enqueue work on `stream`.
+ *
+ * rf_unet_conv3x3: y = act(conv3x3_same(x, w) + bias), w [Cout][3][3][Cin],
+ *   bias [Cout] FP32 (nullable), relu 0/1, y [B][H][W][Cout] BF16, y32
+ *   (nullable) the same values in FP32.  Implicit GEMM on the tensor cores.
+ *   With w replaced by rf_unet_flip_weights(w) it computes the data
+ *   gradient dx from dy. */
+rf_status rf_unet_conv3x3(rf_ctx *ctx, const uint16_t *x, int B, int H, int W,
+                          int Cin, const uint16_t *w, const float *bias,
+                          int Cout, int relu, uint16_t *y, float *y32,
+                          void *stream);
+/* dw [Cout][3][3][Cin] (FP32) += sum over pixels of dy (x) im2col(x): the
+ * weight gradient; the caller zeroes dw. */
+rf_status rf_unet_conv3x3_wgrad(rf_ctx *ctx, const uint16_t *x,
+                                const uint16_t *dy, int B, int H, int W,
+                                int Cin, int Cout, float *dw, void *stream);
+/* db [C] (FP32) += sum over npix pixels of dy [npix][C]. */
+rf_status rf_unet_bias_grad(rf_ctx *ctx, const uint16_t *dy, int64_t npix,
+                            int C, float *db, void *stream);
+/* wt [Cin][3][3][Cout] = w [Cout][3][3][Cin] flipped in both spatial axes:
+ * the weights of the data-gradient convolution. */
+rf_status rf_unet_flip_weights(rf_ctx *ctx, const uint16_t *w, int Cin,
+                               int Cout, uint16_t *wt, void *stream);
+/* 2x2 max pooling (H, W even): y [B][H/2][W/2][C], arg = argmax 0..3 per
+ * output; the backward scatters dy to the argmax positions (dx fully
+ * written). */
+rf_status rf_unet_maxpool2(rf_ctx *ctx, const uint16_t *x, int B, int H,
+                           int W, int C, uint16_t *y, uint8_t *arg,
+                           void *stream);
+rf_status rf_unet_maxpool2_backward(rf_ctx *ctx, const uint16_t *dy,
+                                    const uint8_t *arg, int B, int H, int W,
+                                    int C, uint16_t *dx, void *stream);
+/* Nearest 2x upsampling of x [B][H][W][C] to y [B][2H][2W][C]; the
+ * backward sums the four children into dx [B][H][W][C]. */
+rf_status rf_unet_upsample2(rf_ctx *ctx, const uint16_t *x, int B, int H,
+                            int W, int C, uint16_t *y, void *stream);
+rf_status rf_unet_upsample2_backward(rf_ctx *ctx, const uint16_t *dy, int B,
+                                     int H, int W, int C, uint16_t *dx,
+                                     void *stream);
+/* split == 0: y [npix][Ca+Cb] = concat(a [npix][Ca], b [npix][Cb]) along
+ * channels; split == 1: the reverse copy (the backward). */
+rf_status rf_unet_concat(rf_ctx *ctx, uint16_t *a, int Ca, uint16_t *b,
+                         int Cb, int64_t npix, uint16_t *y, int split,
+                         void *stream);
+/* dy[i] = 0 where y[i] <= 0 (backward of a ReLU whose output is y). */
+rf_status rf_unet_relu_backward(rf_ctx *ctx, uint16_t *dy, const uint16_t *y,
+                                int64_t n, void *stream);
+/* Masked mean-squared error on channel 0 of pred32 [npix][C]:
+ * loss += sum m (p - t)^2 / count; dpred [npix][C] = 2 m (p - t) / count on
+ * channel 0 and 0 elsewhere.  mask nullable (all ones). */
+rf_status rf_unet_mse(rf_ctx *ctx, const float *pred32, int C,
+                      const float *target, const float *mask, int64_t npix,
+                      float count, uint16_t *dpred, float *loss,
+                      void *stream);
+/* y = bf16(x), round to nearest even. */
+rf_status rf_unet_cast_bf16(rf_ctx *ctx, const float *x, uint16_t *y,
+                            int64_t n, void *stream);
+/* planes [B][Cp][H][W] FP32 -> y [B][H][W][C] BF16, channels >= Cp zero. */
+rf_status rf_unet_pack_input(rf_ctx *ctx, const float *planes, int Cp, int B,
+                             int H, int W, int C, uint16_t *y, void *stream);
+
+/* y += x, n BF16 values (FP32 arithmetic): joins skip gradients. */
+rf_status rf_unet_add(rf_ctx *ctx, uint16_t *y, const uint16_t *x, int64_t n,
+                      void *stream);
+/* Network input features: for every pixel of image b, the distance to the
+ * nearest source and the displacement (x, y) to it, in domain units (h per
+ * pixel); out [B][3][H][W] FP32.  src_ij [nsrc][2] (row, column) device
+ * int32, grouped by image: image b owns entries src_off[b] ..
+ * src_off[b+1] - 1 (src_off [B+1]). */
+rf_status rf_unet_source_features(rf_ctx *ctx, int B, int H, int W, float h,
+                                  const int32_t *src_ij,
+                                  const int32_t *src_off, float *out,
+                                  void *stream);
+/* Box average of FP32 planes x [P][H][W] by an integer factor f (H, W
+ * divisible by f) into y [P][H/f][W/f]. */
+rf_status rf_unet_box_down(rf_ctx *ctx, const float *x, int P, int H, int W,
+                           int f, float *y, void *stream);
+/* Node-aligned bilinear resampling of FP32 planes x [P][Hi][Wi] into
+ * y [P][Ho][Wo] (corners map to corners), multiplied by scale. */
+rf_status rf_unet_bilinear(rf_ctx *ctx, const float *x, int P, int Hi,
+                           int Wi, int Ho, int Wo, float scale, float *y,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,26 @@ def load(path: str = LIB_PATH):
         "rf_sweep_forward_static": [ctypes.POINTER(Grid), P, F, P, ctypes.POINTER(Opts), P,
                                     ctypes.POINTER(Stats), P],
     }
+    I64 = ctypes.c_int64
+    sig.update({
+        "rf_unet_conv3x3": [P, P, I, I, I, I, P, P, I, I, P, P, P],
+        "rf_unet_conv3x3_wgrad": [P, P, P, I, I, I, I, I, P, P],
+        "rf_unet_bias_grad": [P, P, I64, I, P, P],
+        "rf_unet_flip_weights": [P, P, I, I, P, P],
+        "rf_unet_maxpool2": [P, P, I, I, I, I, P, P, P],
+        "rf_unet_maxpool2_backward": [P, P, P, I, I, I, I, P, P],
+        "rf_unet_upsample2": [P, P, I, I, I, I, P, P],
+        "rf_unet_upsample2_backward": [P, P, I, I, I, I, P, P],
+        "rf_unet_concat": [P, P, I, P, I, I64, P, I, P],
+        "rf_unet_relu_backward": [P, P, P, I64, P],
+        "rf_unet_mse": [P, P, I, P, P, I64, F, P, P, P],
+        "rf_unet_cast_bf16": [P, P, P, I64, P],
+        "rf_unet_pack_input": [P, P, I, I, I, I, I, P, P],
+        "rf_unet_add": [P, P, P, I64, P],
+        "rf_unet_source_features": [P, I, I, I, F, P, P, P, P],
+        "rf_unet_box_down": [P, P, I, I, I, I, P, P],
+        "rf_unet_bilinear": [P, P, I, I, I, I, I, F, P, P],
+    })
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args

@@ -1,0 +1,68 @@
+"""Learned warm start: the batched training-data solver, the replacement
+(non-min) warm update, and a trained network's warm start, all judged
+against the cold solve and the residual check."""
+import numpy as np
+import pytest
+
+import rf_inputs as R
+from gpu_util import FWD_TOL, require_gpu, to_dev, torch
+from paper_2603_00035_gb300 import api, warmstart as WS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def test_batch_forward_matches_single_grid():
+    x, T, gstat = WS.make_samples([11, 12, 13], n=64)
+    assert int(gstat[:, 0].abs().sum()) == 0
+    assert x.shape == (3, 64, 64, 16) and x.dtype == torch.bfloat16
+    from rf_inputs import gpu as G
+    h = 1.0 / 63
+    for b, seed in enumerate([11, 12, 13]):
+        raw = G.randers_fields_batch([seed], 64, h, 8 if seed % 2 == 0 else 16)[0].contiguous()
+        src, _ = G.random_sources_batch([seed], 64)
+        proj, _ = api.rf_project(raw, 1e-6, 0.05)
+        Tr, _ = api.rf_sweep_forward(proj, 1e-6, src[0].contiguous(), h, record=False)
+        assert (T[b] - Tr).abs().max().item() <= 1e-6 * Tr.max().item()
+
+
+@pytest.mark.parametrize("scale,which", [(0.5, "config1"), (1.3, "config2")])
+def test_replacement_update_recovers_from_bad_guesses(scale, which):
+    """Warm starts from a guess below (0.5 T) or above (1.3 T) the solution
+    reach the cold solution: an underestimate cannot freeze in (it rises
+    about one edge cost per sweep, so the underestimate case uses the small
+    grid and a larger sweep cap)."""
+    c = R.config1() if which == "config1" else R.config2()
+    proj, _ = api.rf_project(to_dev(c["raw"], torch.float32), c["eps"], c["delta"])
+    src = to_dev(c["src"], torch.uint8)
+    Tc, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], record=False)
+    T0 = (Tc * scale).contiguous()
+    Tw, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], opts=api.make_opts(warm=True, max_sweeps=1000),
+                                 T=T0, record=False)
+    st = api.Context.get(0).stats()
+    assert st["status"] == 0 and st["converged"], st
+    assert (Tw - Tc).abs().max().item() <= FWD_TOL * Tc.max().item()
+
+
+def test_trained_network_warm_start_is_correct_and_measured():
+    """Train briefly on solver-generated samples, warm-start a 1024^2 solve,
+    and check it against the cold solve and the residual test.  The sweep
+    counts of both are printed: that is the measured gain (it may be small:
+    the sweep count is set by how often characteristics turn)."""
+    net, tr = WS.train(samples=128, chunk=64, batch=8)
+    assert tr["loss_history"][-1] < tr["loss_history"][0]
+    n = 1024
+    h = 1.0 / (n - 1)
+    raw = torch.from_numpy(R.randers_fields(n, n, h, 16, 77, omega="unit", omega_scale=0.3)).cuda()
+    src = torch.from_numpy(R.random_sources(n, n, 3, 77)).cuda()
+    proj, _ = api.rf_project(raw, 1e-6, 0.05)
+    Tc, _ = api.rf_sweep_forward(proj, 1e-6, src, h, record=False)
+    stc = api.Context.get(0).stats()
+    Tw, info = WS.solve(net, raw, src, h)
+    assert (Tw - Tc).abs().max().item() <= FWD_TOL * Tc.max().item()
+    assert info["residual"] <= 1e-5 * Tc.max().item() or info["fallback"]
+    print(f"cold sweeps {stc['sweeps']}, warm sweeps {info['warm_sweeps']}, fallback {info['fallback']}")
