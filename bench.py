@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--algo", default="ordered", choices=["sweep", "ordered"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--block", type=int, default=0)
+    p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 4])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256"],
@@ -201,14 +202,14 @@ def run_ours(args):
     src = torch.from_numpy(c["src"]).to(dev)
     g = torch.from_numpy(c["g"]).to(dev)
     ctx = api.Context.get(local)
-    tile = {"band": args.band, "block": args.block, "autotuned": False}
-    if not (args.band and args.block):
+    tile = {"band": args.band, "block": args.block, "variant": args.variant, "autotuned": False}
+    if not (args.band and args.block and args.variant):
         from paper_2603_00035_gb300 import autotune
         proj0, _ = api.rf_project(raw, eps, delta)
-        b_, k_ = autotune.tune_sweep(proj0, eps, src, h)
-        tile = {"band": b_, "block": k_, "autotuned": True, "cache": autotune.cache_path()}
+        b_, k_, n_ = autotune.tune_sweep(proj0, eps, src, h)
+        tile = {"band": b_, "block": k_, "variant": n_, "autotuned": True, "cache": autotune.cache_path()}
         del proj0
-    opts = api.make_opts(band=tile["band"], block=tile["block"])
+    opts = api.make_opts(band=tile["band"], block=tile["block"], variant=tile["variant"])
     stream = torch.cuda.current_stream()
     # preallocated outputs: the timed steps allocate nothing
     proj = torch.empty_like(raw)

@@ -64,6 +64,25 @@ enum rf_adjoint_algo {
   RF_ADJ_ORDERED = 1 /* radix sort on T, then dependency-ordered gather     */
 };
 
+/* Forward-sweep kernel variants (all run the same schedule and update;
+ * they differ in how a line step gets its per-node constants).
+ *  TILED1    node tables built per block in shared memory, one thread per
+ *            node evaluates all 16 candidates;
+ *  STREAMED  node records (24 floats) computed once per solve into a
+ *            device buffer of 192 bytes per node owned by the context, and
+ *            copied per line step by the bulk-copy engine; one thread per
+ *            node, two-point candidates in the cone form (same values up to
+ *            FP32 rounding);
+ *  TILED4    as TILED1 with four threads per node and a shuffle minimum.
+ * AUTO = STREAMED when its shape fits the device and the record buffer can
+ * be allocated, else TILED1. */
+enum rf_sweep_variant {
+  RF_SWEEP_AUTO = 0,
+  RF_SWEEP_TILED1 = 1,
+  RF_SWEEP_STREAMED = 2,
+  RF_SWEEP_TILED4 = 4
+};
+
 typedef struct rf_opts {
   float tol;          /* absolute part of the change test (see rtol)        */
   int32_t max_sweeps; /* cap on directional sweeps (4 per iteration)       */
@@ -77,6 +96,7 @@ typedef struct rf_opts {
                          0 asks for bitwise no-change, which FP32 rounding
                          can turn into an ulp-level 2-cycle; the default
                          (opts NULL) is tol 0, rtol 1e-6 (about 8 ulp)     */
+  int32_t variant;    /* enum rf_sweep_variant (0 = auto)                   */
 } rf_opts;
 
 /* Per-node record of the converged forward solve (Alg. 2, first loop). */

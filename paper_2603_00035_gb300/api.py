@@ -122,11 +122,18 @@ def rf_project_backward(raw5, clip, eps, delta, dproj5, draw5=None, ctx=None, st
     return draw5
 
 
-def make_opts(tol=0.0, max_sweeps=64, warm=False, band=0, block=0, rtol=1e-6):
+SWEEP_VARIANTS = {"auto": L.RF_SWEEP_AUTO, "tiled1": L.RF_SWEEP_TILED1, "streamed": L.RF_SWEEP_STREAMED,
+                  "tiled4": L.RF_SWEEP_TILED4}
+
+
+def make_opts(tol=0.0, max_sweeps=64, warm=False, band=0, block=0, rtol=1e-6, variant=0):
     """rf_opts: a node counts as changed when |dT| > tol + rtol * T (tol =
-    rtol = 0: bitwise); the sweep stops at the first sweep with no change."""
+    rtol = 0: bitwise); the sweep stops at the first sweep with no change.
+    band/block: line-tile shape (0 = auto); variant: forward-sweep kernel,
+    a name of SWEEP_VARIANTS or its value (0 = auto)."""
+    v = SWEEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
     return L.Opts(float(tol), int(max_sweeps), L.RF_MODE_WARM if warm else L.RF_MODE_COLD, int(band), int(block),
-                  float(rtol))
+                  float(rtol), v)
 
 
 def rf_sweep_forward(proj5, eps, src, h, opts=None, T=None, record=True, rec=None, ctx=None, stream=None):

@@ -1,11 +1,13 @@
 """Autotuner for the line-tile shape of the forward sweep.
 
 rf_sweep_forward splits every sweep's lines into bands of R lines (one CTA
-each) and advances a band K line steps per block (halo of K lines).  The
-best (R, K) depends on the grid size and the GPU.  tune_sweep() times the
-candidate shapes on a real solve and keeps the fastest per grid-size bucket
-(next power of two of max(ny, nx)); results are cached in a JSON file keyed
-by the GPU name, so later processes reuse them without timing again.
+each) and advances a band K line steps per block (halo of K lines), with
+one of the kernel variants of rf_sweep_variant.  The best (R, K, variant)
+depends on the grid size and the GPU.  tune_sweep() times the candidate
+shapes on a real solve and keeps the fastest per grid-size bucket (next
+power of two of max(ny, nx)); results are cached in a JSON file keyed by
+the GPU name, so later processes reuse them without timing again.  Cache
+entries without a variant field (written before it existed) are ignored.
 
 Cache file: $RF_AUTOTUNE_CACHE, else ~/.cache/rf_gb300/autotune.json.
 """
@@ -15,7 +17,9 @@ import json
 import os
 import threading
 
-CANDIDATES = [(32, 32), (16, 16), (32, 16), (48, 16), (64, 32), (24, 8)]
+# (band, block, variant): 2 streamed, 1 tiled with one thread per node, 4 tiled with four
+CANDIDATES = [(32, 32, 2), (64, 16, 2), (32, 16, 2), (16, 16, 2), (32, 32, 1), (16, 16, 1), (32, 16, 1),
+              (32, 32, 4)]
 
 _lock = threading.Lock()
 
@@ -53,22 +57,25 @@ def _store(d: dict) -> None:
 
 
 def lookup(device_name: str, ny: int, nx: int):
-    """(band, block) cached for this GPU and size bucket, or None."""
+    """(band, block, variant) cached for this GPU and size bucket, or None."""
     with _lock:
         e = _load().get(device_name, {}).get(str(bucket(ny, nx)))
-    return (int(e["band"]), int(e["block"])) if e else None
+    if not e or "variant" not in e:
+        return None
+    return (int(e["band"]), int(e["block"]), int(e["variant"]))
 
 
-def record(device_name: str, ny: int, nx: int, band: int, block: int, ms: float, table=None) -> None:
+def record(device_name: str, ny: int, nx: int, band: int, block: int, variant: int, ms: float, table=None) -> None:
     with _lock:
         d = _load()
         d.setdefault(device_name, {})[str(bucket(ny, nx))] = {"band": int(band), "block": int(block),
-                                                              "ms": float(ms), "timings": table or {}}
+                                                              "variant": int(variant), "ms": float(ms),
+                                                              "timings": table or {}}
         _store(d)
 
 
 def choose(timings: dict):
-    """Fastest (band, block) of {(band, block): ms}; ties go to the first."""
+    """Fastest shape of {shape: ms}; ties go to the first."""
     best = None
     for shape, ms in timings.items():
         if best is None or ms < timings[best]:
@@ -77,8 +84,9 @@ def choose(timings: dict):
 
 
 def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
-    """Time rf_sweep_forward for each candidate (band, block) on this input,
-    cache and return the fastest.  Uses the cached result unless force."""
+    """Time rf_sweep_forward for each candidate (band, block, variant) on this
+    input, cache and return the fastest.  Uses the cached result unless
+    force."""
     import torch
 
     from . import api
@@ -92,8 +100,8 @@ def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
     T = torch.empty((ny, nx), dtype=torch.float32, device=proj5.device)
     timings = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for band, block in (candidates or CANDIDATES):
-        o = api.make_opts(band=band, block=block)
+    for band, block, variant in (candidates or CANDIDATES):
+        o = api.make_opts(band=band, block=block, variant=variant)
         try:
             api.rf_sweep_forward(proj5, eps, src, h, opts=o, T=T, record=False)
         except Exception:
@@ -104,10 +112,10 @@ def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
             api.rf_sweep_forward(proj5, eps, src, h, opts=o, T=T, record=False)
         e1.record()
         torch.cuda.synchronize()
-        timings[(band, block)] = e0.elapsed_time(e1) / repeats
+        timings[(band, block, variant)] = e0.elapsed_time(e1) / repeats
     api.Context.get(proj5.device).stats()
     best = choose(timings)
-    record(name, ny, nx, best[0], best[1], timings[best], {f"{b}x{k}": round(v, 4) for (b, k), v in timings.items()})
+    record(name, ny, nx, *best, timings[best], {f"{b}x{k}x{n}": round(v, 4) for (b, k, n), v in timings.items()})
     return best
 
 
@@ -118,4 +126,5 @@ def best_opts(device_name: str, ny: int, nx: int, **kw):
     if hit is not None:
         kw.setdefault("band", hit[0])
         kw.setdefault("block", hit[1])
+        kw.setdefault("variant", hit[2])
     return api.make_opts(**kw)

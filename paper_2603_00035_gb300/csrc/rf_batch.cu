@@ -359,7 +359,7 @@ extern "C" rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int
     return RF_ERR_INVALID_ARG;
   if (max_line < 1 || max_line > kBThreads * kBCells || !(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
   if (dLdT && !dLdproj5) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0};
   if (opts) o = *opts;
   if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
     return RF_ERR_INVALID_ARG;

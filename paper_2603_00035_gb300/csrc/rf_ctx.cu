@@ -37,6 +37,7 @@ extern "C" rf_status rf_ctx_destroy(rf_ctx *c) {
   cudaFree(c->lbuf);
   cudaFree(c->scratch);
   cudaFree(c->adj_state);
+  cudaFree(c->recbuf);
   delete c;
   return RF_OK;
 }

@@ -30,6 +30,8 @@ struct rf_ctx {
   unsigned long long *adj_state = nullptr;  // adjoint (ordered): (epoch << 32 | lambda bits)
   size_t adj_state_cap = 0;
   unsigned adj_epoch = 0;  // launch counter tagging adj_state words
+  float4 *recbuf = nullptr;  // streamed sweep: node records, both orientations
+  size_t recbuf_cap = 0;
 };
 
 namespace rf {

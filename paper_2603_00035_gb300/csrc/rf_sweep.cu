@@ -29,6 +29,7 @@
 
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
+#include "rf_sweep_stream.h"
 
 namespace rf {
 
@@ -48,37 +49,98 @@ struct SweepArgs {
   LaunchCtl ctl;
 };
 
-// Lanes per node in the line-step loop: lane q of a node evaluates the
-// two-point candidates of stencils 2q, 2q+1 and the one-point candidates of
-// neighbours 2q, 2q+1; a two-level shuffle takes the minimum.
+// Lanes per node in the line-step loop (template parameter NL):
+//  NL = 4: lane q of a node evaluates the two-point candidates of stencils
+//          2q, 2q+1 and the one-point candidates of neighbours 2q, 2q+1; a
+//          two-level shuffle takes the minimum.  Node tables are kTabSize
+//          planes of K x EP floats plus K x EP source bytes.
+//  NL = 1: one thread evaluates all 16 candidates of its node (no shuffles,
+//          each table value and donor time loaded once).  Node tables are
+//          K x EP records of kRec floats (the 11 table values and the source
+//          flag), read as three float4; the 48-byte record stride puts the
+//          8 threads of a quarter-warp on distinct banks.  Only the first
+//          ext threads step; the others stage and publish.
+// Both use 4 * ext threads, so staging and publishing cost the same.
 constexpr int kLanes = 4;
+constexpr int kRec = 12;
 constexpr int kMaxExt = 128;    // R + 2K <= 128  ->  <= 512 threads
+constexpr int kMaxExt1 = 96;    // NL = 1: <= 384 threads (168 registers)
 constexpr int kMaxTabPer = 8;   // node tables staged per thread per block (K/4)
 constexpr int kMaxOldPer = 12;  // old-T values staged per thread per block
 
+template <int NL>
 __host__ __device__ inline size_t sweep_smem_bytes(int R, int K) {
   const int ext = R + 2 * K, W = ext + 2, P = W | 1, EP = ext | 1;
-  size_t fl = (size_t)(K + 2) * P + (size_t)(K + 1) * P + (size_t)kTabSize * K * EP;
-  return fl * sizeof(float) + (size_t)K * EP;
+  const size_t tfl = (size_t)(K + 2) * P + (size_t)(K + 1) * P;
+  if (NL == 1) return ((size_t)kRec * K * EP + tfl) * sizeof(float);
+  return (tfl + (size_t)kTabSize * K * EP) * sizeof(float) + (size_t)K * EP;
 }
 
 __host__ __device__ inline int sweep_threads(int R, int K) { return kLanes * (R + 2 * K); }
 
-// Shapes the kernel accepts: K a power of two <= 32, R >= K, R + 2K <= 128,
-// and the staged values per thread within the register budget.
-__host__ inline bool sweep_shape_ok(int R, int K) {
-  if (K < 4 || K > 32 || (K & (K - 1)) || R < K || R + 2 * K > kMaxExt) return false;
+// Shapes the kernel accepts: K a power of two <= 32, R >= K, R + 2K <= 128
+// (96 for NL = 1), and the staged values per thread within the register
+// budget.
+__host__ inline bool sweep_shape_ok(int R, int K, int NL) {
+  if (K < 4 || K > 32 || (K & (K - 1)) || R < K || R + 2 * K > (NL == 1 ? kMaxExt1 : kMaxExt)) return false;
   const int nth = sweep_threads(R, K), W = R + 2 * K + 2;
   return (K * (R + 2 * K) + nth - 1) / nth <= kMaxTabPer && ((K + 2) * W + nth - 1) / nth <= kMaxOldPer;
 }
 
-__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
-  extern __shared__ float smem[];
+// K line steps of one block, one thread per node (NL = 1).  Thread e owns
+// tile line e; at step t it needs the donors of step t-1 of this sweep
+// (nw row t) and of steps t, t+1 before the sweep (old rows t+1, t+2).
+// Returns whether an inner node changed.
+template <int DIR>
+__device__ __forceinline__ int steps_one_lane(const float *__restrict__ tb, const float *__restrict__ old, float *nw,
+                                              int P, int EP, int K, int R, int ext, int t_end, int l0, int L,
+                                              float tol, float rtol) {
+  const int e = threadIdx.x, tl = e + 1, l = l0 - K + e;
+  const bool valid = (e < ext) && (l >= 0) && (l < L);
+  const bool inband = (e >= K) && (e < K + R);
+  int changed = 0;
+  for (int t = 0; t < t_end; ++t) {
+    // only nodes e in [t+1, ext-1-t) can still influence the inner lines
+    if (e < ext && e > t && e < ext - 1 - t) {
+      float Tn[8];
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const int ds = tile_ds<DIR>(n), dl = tile_dl<DIR>(n);
+        Tn[n] = (ds < 0) ? nw[t * P + tl + dl] : old[(t + 1 + ds) * P + tl + dl];
+      }
+      const float4 *rp = reinterpret_cast<const float4 *>(tb + (size_t)(t * EP + e) * kRec);
+      const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2];
+      const float tab[kTabSize] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z};
+      float cand = kInf;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        float l1, l2;
+        cand = fminf(cand, two_point(tab, k, Tn[k], Tn[(k + 1) & 7], l1, l2));
+      }
+#pragma unroll
+      for (int n = 0; n < 8; ++n) cand = fminf(cand, one_point(tab, n, Tn[n]));
+      float tnew = kInf;
+      if (valid) {
+        tnew = (r2.w != 0.0f) ? 0.0f : cand;
+        if (inband) changed |= node_changed(tnew, old[(t + 1) * P + tl], tol, rtol);
+      }
+      nw[(t + 1) * P + tl] = tnew;
+    }
+    __syncthreads();
+  }
+  return changed;
+}
+
+template <int NL>
+__global__ void __launch_bounds__(NL == 1 ? 384 : 512) sweep_kernel(SweepArgs a) {
+  extern __shared__ float4 smem4[];
+  float *smem = reinterpret_cast<float *>(smem4);
   const int R = a.R, K = a.K, ext = R + 2 * K, W = ext + 2, P = W | 1, EP = ext | 1;
-  float *old = smem;                                  // (K+2) x P  T before the sweep
-  float *nw = old + (size_t)(K + 2) * P;              // (K+1) x P  T of this sweep
-  float *tb = nw + (size_t)(K + 1) * P;               // kTabSize x K x EP node tables
-  uint8_t *sm = (uint8_t *)(tb + (size_t)kTabSize * K * EP);  // K x EP source flags
+  // NL = 1: records first (16-byte aligned), then old and nw
+  float *tb = (NL == 1) ? smem : smem + (size_t)(2 * K + 3) * P;  // node tables
+  float *old = (NL == 1) ? smem + (size_t)kRec * K * EP : smem;   // (K+2) x P  T before the sweep
+  float *nw = old + (size_t)(K + 2) * P;                          // (K+1) x P  T of this sweep
+  uint8_t *sm = (uint8_t *)(smem + (size_t)(2 * K + 3) * P + (size_t)kTabSize * K * EP);  // NL = 4: source flags
   const int TS = K * EP;                              // table plane stride
   __shared__ int s_ok;
   __shared__ int s_any;
@@ -173,9 +235,16 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
           const int t = tabidx[j] & 255, e = tabidx[j] >> 8;
           float tab[kTabSize];
           node_tab(rv[j][0], rv[j][1], rv[j][2], rv[j][3], rv[j][4], a.h, a.eps, tab);
+          if (NL == 1) {
+            float4 *d = reinterpret_cast<float4 *>(tb + (size_t)(t * EP + e) * kRec);
+            d[0] = make_float4(tab[0], tab[1], tab[2], tab[3]);
+            d[1] = make_float4(tab[4], tab[5], tab[6], tab[7]);
+            d[2] = make_float4(tab[8], tab[9], tab[10], sv[j] ? 1.0f : 0.0f);
+          } else {
 #pragma unroll
-          for (int c = 0; c < kTabSize; ++c) tb[c * TS + t * EP + e] = tab[c];
-          sm[t * EP + e] = sv[j];
+            for (int c = 0; c < kTabSize; ++c) tb[c * TS + t * EP + e] = tab[c];
+            sm[t * EP + e] = sv[j];
+          }
         }
 #pragma unroll
         for (int j = 0; j < kMaxOldPer; ++j) {
@@ -214,44 +283,54 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
         __syncthreads();
         // 4. K line steps, one parallel front each.  At step t only nodes
         // e in [t+1, ext-1-t) can still influence the inner lines.
-        for (int t = 0; t < K; ++t) {
-          const int s = s0 + t;
-          if (s >= S) break;
-          const int e = cell, tl = e + 1, l = l0 - K + e;
-          const bool need = (e > t) && (e < ext - 1 - t);
-          if (__any_sync(0xffffffffu, need)) {
-            const bool live = need && (l >= 0) && (l < L);
-            float cand = kInf;
-            if (live) {
-              float Tq[3];
-#pragma unroll
-              for (int u = 0; u < 3; ++u)
-                Tq[u] = (nds[u] < 0) ? nw[t * P + tl + ndl[u]] : old[(t + 1 + nds[u]) * P + tl + ndl[u]];
-              const float *tc = tb + t * EP + e;
-              const float len0 = tc[offL0], len1 = tc[offL1], len2 = tc[offL2];
-              const float w0 = sg0 * tc[offW0], w1 = sg1 * tc[offW1], w2 = sg2 * tc[offW2];
-              const float lx = tc[offLx], aa = lx * lx, inv = tc[offInv], det = tc[offDet];
-              float l1, l2;
-              cand = two_point_core(len0, len1, w0, w1, aa, inv, det, Tq[0], Tq[1], l1, l2);
-              cand = fminf(cand, two_point_core(len1, len2, w1, w2, aa, inv, det, Tq[1], Tq[2], l1, l2));
-              cand = fminf(cand, one_point_core(len0, w0, Tq[0]));
-              cand = fminf(cand, one_point_core(len1, w1, Tq[1]));
-            }
-            cand = fminf(cand, __shfl_xor_sync(0xffffffffu, cand, 1));
-            cand = fminf(cand, __shfl_xor_sync(0xffffffffu, cand, 2));
-            if (q == 0 && need) {
-              float tnew = kInf;
-              if (live) {
-                const float told = old[(t + 1) * P + tl];
-                tnew = sm[t * EP + e] ? 0.0f : cand;
-                if (e >= K && e < K + R) {
-                  local_changed |= node_changed(tnew, told, a.tol, a.rtol);
-                }
-              }
-              nw[(t + 1) * P + tl] = tnew;
-            }
+        if (NL == 1) {
+          const int t_end = min(K, S - s0);
+          switch (dir) {
+            case 0: local_changed |= steps_one_lane<0>(tb, old, nw, P, EP, K, R, ext, t_end, l0, L, a.tol, a.rtol); break;
+            case 1: local_changed |= steps_one_lane<1>(tb, old, nw, P, EP, K, R, ext, t_end, l0, L, a.tol, a.rtol); break;
+            case 2: local_changed |= steps_one_lane<2>(tb, old, nw, P, EP, K, R, ext, t_end, l0, L, a.tol, a.rtol); break;
+            default: local_changed |= steps_one_lane<3>(tb, old, nw, P, EP, K, R, ext, t_end, l0, L, a.tol, a.rtol); break;
           }
-          __syncthreads();
+        } else {
+          for (int t = 0; t < K; ++t) {
+            const int s = s0 + t;
+            if (s >= S) break;
+            const int e = cell, tl = e + 1, l = l0 - K + e;
+            const bool need = (e > t) && (e < ext - 1 - t);
+            if (__any_sync(0xffffffffu, need)) {
+              const bool live = need && (l >= 0) && (l < L);
+              float cand = kInf;
+              if (live) {
+                float Tq[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+                  Tq[u] = (nds[u] < 0) ? nw[t * P + tl + ndl[u]] : old[(t + 1 + nds[u]) * P + tl + ndl[u]];
+                const float *tc = tb + t * EP + e;
+                const float len0 = tc[offL0], len1 = tc[offL1], len2 = tc[offL2];
+                const float w0 = sg0 * tc[offW0], w1 = sg1 * tc[offW1], w2 = sg2 * tc[offW2];
+                const float lx = tc[offLx], aa = lx * lx, inv = tc[offInv], det = tc[offDet];
+                float l1, l2;
+                cand = two_point_core(len0, len1, w0, w1, aa, inv, det, Tq[0], Tq[1], l1, l2);
+                cand = fminf(cand, two_point_core(len1, len2, w1, w2, aa, inv, det, Tq[1], Tq[2], l1, l2));
+                cand = fminf(cand, one_point_core(len0, w0, Tq[0]));
+                cand = fminf(cand, one_point_core(len1, w1, Tq[1]));
+              }
+              cand = fminf(cand, __shfl_xor_sync(0xffffffffu, cand, 1));
+              cand = fminf(cand, __shfl_xor_sync(0xffffffffu, cand, 2));
+              if (q == 0 && need) {
+                float tnew = kInf;
+                if (live) {
+                  const float told = old[(t + 1) * P + tl];
+                  tnew = sm[t * EP + e] ? 0.0f : cand;
+                  if (e >= K && e < K + R) {
+                    local_changed |= node_changed(tnew, told, a.tol, a.rtol);
+                  }
+                }
+                nw[(t + 1) * P + tl] = tnew;
+              }
+            }
+            __syncthreads();
+          }
         }
         // 5. publish the inner lines, prefetch the next block, then release
         const int nwarps = nth >> 5, warp = tid >> 5, lane = tid & 31;
@@ -386,39 +465,53 @@ using namespace rf;
 namespace {
 
 struct SweepPlan {
-  int R, K, grid, threads;
+  int R, K, NL, grid, threads;
   size_t smem;
+  const void *kernel;
 };
 
-rf_status plan_sweep(rf_ctx *ctx, int ny, int nx, const rf_opts *o, SweepPlan *pl) {
-  int K = (o && o->block > 0) ? o->block : 32;
-  int R = (o && o->band > 0) ? o->band : 32;
-  // round the requested shape to one the kernel accepts
-  int k2 = 4;
-  while (k2 * 2 <= K && k2 < 32) k2 *= 2;
-  K = k2;
-  if (R < K) R = K;
-  while (R + 2 * K > kMaxExt && K > 4) K /= 2;
-  if (R + 2 * K > kMaxExt) R = kMaxExt - 2 * K;
-  if (!sweep_shape_ok(R, K)) return RF_ERR_UNSUPPORTED;
-  const int maxL = std::max(ny, nx);
+template <int NL>
+rf_status plan_kernel(rf_ctx *ctx, int R, int K, int maxL, SweepPlan *pl) {
+  if (!sweep_shape_ok(R, K, NL)) return RF_ERR_UNSUPPORTED;
   int dev_max_smem = 0;
   cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   const int threads = sweep_threads(R, K);
-  const size_t smem = sweep_smem_bytes(R, K);
+  const size_t smem = sweep_smem_bytes<NL>(R, K);
   if ((long long)smem > dev_max_smem) return RF_ERR_UNSUPPORTED;
-  cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(sweep_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, threads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<NL>, threads, smem) != cudaSuccess)
     return RF_ERR_CUDA;
   const int grid = (maxL + R - 1) / R;
   if (per_sm < 1 || grid > per_sm * ctx->num_sms) return RF_ERR_UNSUPPORTED;
   pl->R = R;
   pl->K = K;
+  pl->NL = NL;
   pl->grid = grid;
   pl->threads = threads;
   pl->smem = smem;
+  pl->kernel = (const void *)sweep_kernel<NL>;
   return RF_OK;
+}
+
+// Tiled variants (node tables built per block); lanes = 1 or 4.
+rf_status plan_sweep(rf_ctx *ctx, int ny, int nx, const rf_opts *o, int lanes, SweepPlan *pl) {
+  int K = (o && o->block > 0) ? o->block : 32;
+  int R = (o && o->band > 0) ? o->band : 32;
+  const int max_ext = lanes == 1 ? kMaxExt1 : kMaxExt;
+  // round the requested shape to one the kernel accepts
+  int k2 = 4;
+  while (k2 * 2 <= K && k2 < 32) k2 *= 2;
+  K = k2;
+  if (R < K) R = K;
+  while (R + 2 * K > max_ext && K > 4) K /= 2;
+  if (R + 2 * K > max_ext) R = max_ext - 2 * K;
+  const int maxL = std::max(ny, nx);
+  return lanes == 1 ? plan_kernel<1>(ctx, R, K, maxL, pl) : plan_kernel<4>(ctx, R, K, maxL, pl);
+}
+
+bool variant_ok(int v) {
+  return v == RF_SWEEP_AUTO || v == RF_SWEEP_TILED1 || v == RF_SWEEP_STREAMED || v == RF_SWEEP_TILED4;
 }
 
 }  // namespace
@@ -429,7 +522,7 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   if (!ctx || !grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
   if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
   if (rec && (!rec->id || !rec->w1 || !rec->dT)) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0};
   if (opts) o = *opts;
   if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
     return RF_ERR_INVALID_ARG;
@@ -439,17 +532,33 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   const int ny = grid->ny, nx = grid->nx;
   const long long n = (long long)ny * nx;
 
+  if (!variant_ok(o.variant)) return RF_ERR_INVALID_ARG;
+
+  // kernel variant: streamed when requested or automatic and it fits,
+  // else tiled (one or four threads per node)
+  rf::StreamPlan sp;
   SweepPlan pl;
-  rf_status rs = plan_sweep(ctx, ny, nx, &o, &pl);
-  if (rs != RF_OK) return rs;
+  bool streamed = false;
+  rf_status rs = RF_OK;
+  if (o.variant == RF_SWEEP_STREAMED || o.variant == RF_SWEEP_AUTO) {
+    rs = rf::stream_plan(ctx, ny, nx, o.band, o.block, &sp);
+    if (rs == RF_OK) rs = ensure(&ctx->recbuf, &ctx->recbuf_cap, rf::stream_record_floats4(ny, nx));
+    if (rs == RF_OK) streamed = true;
+    else if (o.variant == RF_SWEEP_STREAMED) return rs;
+  }
+  if (!streamed) {
+    rs = plan_sweep(ctx, ny, nx, &o, o.variant == RF_SWEEP_TILED4 ? 4 : 1, &pl);
+    if (rs != RF_OK) return rs;
+  }
+  const int grid_ctas = streamed ? sp.grid : pl.grid;
   if ((rs = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)n)) != RF_OK) return rs;
-  if ((rs = ensure(&ctx->progress, &ctx->progress_cap, (size_t)pl.grid + 1)) != RF_OK) return rs;
+  if ((rs = ensure(&ctx->progress, &ctx->progress_cap, (size_t)grid_ctas + 1)) != RF_OK) return rs;
   // changed flags: [0, max_sweeps) per sweep, then has-source, then abort
   if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2)) != RF_OK) return rs;
 
   // reset the counters this launch uses (status word excluded: it
   // accumulates until rf_ctx_last_stats reads it)
-  cudaMemsetAsync(ctx->progress, 0, sizeof(unsigned) * (pl.grid + 1), s);
+  cudaMemsetAsync(ctx->progress, 0, sizeof(unsigned) * (grid_ctas + 1), s);
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
   cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
   cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 3, s);
@@ -460,30 +569,38 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
                                                                      ctx->state, has_src);
   check_source_kernel<<<1, 32, 0, s>>>(has_src, ctx->state);
 
-  SweepArgs a;
-  a.ny = ny;
-  a.nx = nx;
-  a.h = grid->h;
-  a.eps = eps;
-  a.f = proj5;
-  a.src = src;
-  a.Ta = T;
-  a.Tb = ctx->tbuf;
-  a.R = pl.R;
-  a.K = pl.K;
-  a.max_sweeps = o.max_sweeps;
-  a.tol = o.tol;
-  a.rtol = o.rtol;
-  a.tok_stride = (unsigned)((std::max(ny, nx) + pl.K - 1) / pl.K + 1);
-  a.progress = ctx->progress;
-  a.changed = ctx->changed;
-  a.ctl.st = ctx->state;
-  a.ctl.abort = ctx->changed + o.max_sweeps + 1;
-  a.ctl.timeout_ns = ctx->timeout_ns;
-  void *args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void *)sweep_kernel, dim3(pl.grid), dim3(pl.threads),
-                                              args, pl.smem, s);
-  if (e != cudaSuccess) return RF_ERR_CUDA;
+  LaunchCtl ctl;
+  ctl.st = ctx->state;
+  ctl.abort = ctx->changed + o.max_sweeps + 1;
+  ctl.timeout_ns = ctx->timeout_ns;
+  if (streamed) {
+    if ((rs = rf::stream_records(ny, nx, grid->h, eps, proj5, src, ctx->recbuf, s)) != RF_OK) return rs;
+    if ((rs = rf::stream_launch(sp, ny, nx, ctx->recbuf, T, ctx->tbuf, o.max_sweeps, o.tol, o.rtol, ctx->progress,
+                                ctx->changed, ctl, s)) != RF_OK)
+      return rs;
+  } else {
+    SweepArgs a;
+    a.ny = ny;
+    a.nx = nx;
+    a.h = grid->h;
+    a.eps = eps;
+    a.f = proj5;
+    a.src = src;
+    a.Ta = T;
+    a.Tb = ctx->tbuf;
+    a.R = pl.R;
+    a.K = pl.K;
+    a.max_sweeps = o.max_sweeps;
+    a.tol = o.tol;
+    a.rtol = o.rtol;
+    a.tok_stride = (unsigned)((std::max(ny, nx) + pl.K - 1) / pl.K + 1);
+    a.progress = ctx->progress;
+    a.changed = ctx->changed;
+    a.ctl = ctl;
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, s);
+    if (e != cudaSuccess) return RF_ERR_CUDA;
+  }
 
   if (rec) {
     RecordArgs r;
@@ -603,7 +720,7 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
                                              rf_stats *stats, void *stream) {
   if (!grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
   if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0};
   if (opts) o = *opts;
   if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
     return RF_ERR_INVALID_ARG;
@@ -632,8 +749,11 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
   planner.device = dev;
   if (cudaDeviceGetAttribute(&planner.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return RF_ERR_CUDA;
+  // the streamed variant needs a record buffer: not available without
+  // allocation
+  if (o.variant == RF_SWEEP_STREAMED || !variant_ok(o.variant)) return RF_ERR_INVALID_ARG;
   SweepPlan pl;
-  rf_status rs = plan_sweep(&planner, ny, nx, &o, &pl);
+  rf_status rs = plan_sweep(&planner, ny, nx, &o, o.variant == RF_SWEEP_TILED4 ? 4 : 1, &pl);
   if (rs != RF_OK) return rs;
   if (pl.grid > kStaticMaxBands) return RF_ERR_INVALID_ARG;
 
@@ -674,7 +794,7 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
   a.ctl.abort = changed + o.max_sweeps + 1;
   a.ctl.timeout_ns = 2000000000LL;
   void *args[] = {&a};
-  if (cudaLaunchCooperativeKernel((const void *)sweep_kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, s) !=
+  if (cudaLaunchCooperativeKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, s) !=
       cudaSuccess)
     return RF_ERR_CUDA;
   if (!stats) return RF_OK;

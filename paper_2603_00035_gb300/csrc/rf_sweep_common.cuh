@@ -97,6 +97,16 @@ __device__ __forceinline__ void nb_tile_offset(int dir, int n, int &ds, int &dl)
   }
 }
 
+// Tile offset (step, line) of neighbour n for a compile-time direction.
+template <int DIR>
+__device__ constexpr int tile_ds(int n) {
+  return DIR == 0 ? nb_dx(n) : DIR == 1 ? nb_dy(n) : DIR == 2 ? -nb_dx(n) : -nb_dy(n);
+}
+template <int DIR>
+__device__ constexpr int tile_dl(int n) {
+  return (DIR & 1) == 0 ? nb_dy(n) : nb_dx(n);
+}
+
 // Change test of the forward sweeps: |tnew - told| > tol + rtol * tnew,
 // +inf on exactly one side counts as changed; tol = rtol = 0 is bitwise.
 __device__ __forceinline__ bool node_changed(float tnew, float told, float tol, float rtol) {

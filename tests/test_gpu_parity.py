@@ -199,17 +199,37 @@ def test_timeout_path_returns_cleanly():
         assert ctx.stats()["status"] == 0, algo
 
 
-@pytest.mark.parametrize("band,block", [(32, 8), (64, 32), (128, 16), (16, 16)])
-def test_band_and_block_shapes_agree(band, block):
+@pytest.mark.parametrize("band,block,variant", [(32, 8, 4), (64, 32, 4), (128, 16, 4), (16, 16, 4), (32, 32, 1),
+                                               (16, 16, 1), (64, 16, 1), (24, 4, 1), (128, 32, 1), (32, 32, 2),
+                                               (64, 16, 2), (32, 16, 2), (16, 16, 2), (8, 4, 2)])
+def test_band_and_block_shapes_agree(band, block, variant):
     c = ragged_case()
     prj, _ = O.project(c["raw"], c["eps"], c["delta"])
     To, _, _, _ = O.solve_gs(prj, c["src"], c["h"], c["eps"])
     proj, _ = api.rf_project(to_dev(c["raw"], torch.float32), c["eps"], c["delta"])
     T, _ = api.rf_sweep_forward(proj, c["eps"], to_dev(c["src"], torch.uint8), c["h"],
-                                opts=api.make_opts(band=band, block=block), record=False)
+                                opts=api.make_opts(band=band, block=block, variant=variant), record=False)
     st = api.Context.get(0).stats()
     assert st["status"] == 0 and st["converged"]
     assert np.abs(T.cpu().numpy() - To).max() <= FWD_TOL * To.max()
+
+
+@pytest.mark.parametrize("which", ["config1", "config2"])
+def test_sweep_variants_agree(which):
+    """The kernel variants evaluate the same 16 candidates per node (the
+    streamed one in the cone form); only FP32 rounding differs, so T agrees
+    to a few ulp and the reached sets are identical."""
+    c = CASES[which]()
+    proj, _ = api.rf_project(to_dev(c["raw"], torch.float32), c["eps"], c["delta"])
+    src = to_dev(c["src"], torch.uint8)
+    out = {}
+    for v in ("tiled1", "tiled4", "streamed"):
+        out[v], _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], opts=api.make_opts(variant=v), record=False)
+        st = api.Context.get(0).stats()
+        assert st["status"] == 0 and st["converged"], v
+    for v in ("tiled1", "streamed"):
+        assert torch.equal(torch.isfinite(out[v]), torch.isfinite(out["tiled4"])), v
+        assert (out[v] - out["tiled4"]).abs().max().item() <= 1e-5 * out["tiled4"].max().item(), v
 
 
 @pytest.mark.parametrize("which", ["config1", "config2"])

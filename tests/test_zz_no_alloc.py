@@ -38,7 +38,9 @@ def test_static_entry_matches_allocating_entry_twice():
     raw = to_dev(c["raw"], torch.float32)
     src = to_dev(c["src"], torch.uint8)
     proj, _ = api.rf_project(raw, c["eps"], c["delta"])
-    T_ref, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], record=False)
+    # the entry without allocation runs the tiled kernel (the streamed one
+    # needs a record buffer)
+    T_ref, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], opts=api.make_opts(variant="tiled1"), record=False)
     st_ref = api.Context.get(0).stats()
     assert st_ref["status"] == 0 and st_ref["converged"]
     tmax = T_ref.max().item()
