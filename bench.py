@@ -36,8 +36,10 @@ METRIC = "forward+adjoint solves/s at 2048x2048"
 UNIT = "solves/s"
 ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-update
 # kernels of ours per step: project, init, source check, sweep, record, project backward, plus the
-# adjoint's own kernels (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not counted)
+# adjoint's own kernels (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not counted);
+# the streamed forward variant adds its node-record kernel
 LAUNCHES_PER_STEP = {"sweep": 7, "ordered": 9}
+STREAMED = 2
 
 
 def parse():
@@ -330,7 +332,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": dict(workload_config(n), tile=tile),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP[args.algo] * args.steps,
+            "roofline": roofline, "e2e": e2e,
+            "gpu_launches": (LAUNCHES_PER_STEP[args.algo] + (tile["variant"] in (0, STREAMED))) * args.steps,
             "clocks": sampler.summary(),
             "solver": {"sweeps": sweeps, "adj_sweeps": adj_sweeps, "cell_updates": cell_updates,
                        "gcell_updates_per_s": cell_updates / (phase_ms[1] / 1e3) / 1e9,
