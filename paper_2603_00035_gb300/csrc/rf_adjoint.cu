@@ -275,9 +275,13 @@ struct OrderedArgs {
   LaunchCtl ctl;
 };
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+// Polling load: the child's multiplier and the epoch tag sit in one 64-bit
+// word written by one release store, so a relaxed (single-copy atomic)
+// load that sees the tag sees the value; unlike an acquire load it does
+// not hold back the loads of the other children.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
@@ -324,6 +328,7 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
       }
     }
     const unsigned long long t0 = gtimer();
+    unsigned spins = 0;
     while (!__all_sync(0xffffffffu, done)) {
       if (!done) {
         bool ready = true;
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
         for (int nb = 0; nb < 8; ++nb) {
           if (cmask & (1u << nb)) {
             const long long qn = (long long)(pi + nb_dy(nb)) * a.nx + (pj + nb_dx(nb));
-            const unsigned long long v = ld_acquire_u64(&a.state[qn]);
+            const unsigned long long v = ld_relaxed_u64(&a.state[qn]);
             ready = ready && ((v & 0xffffffff00000000ull) == tag);
             acc = fmaf(cw[nb], __uint_as_float((unsigned)v), acc);
           }
@@ -344,7 +349,10 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
           for (int c = 0; c < 5; ++c) a.grad[c * n + p] = act ? acc * a.dT[c * n + p] : 0.0f;
           if (a.lam_out) a.lam_out[p] = acc;
           done = true;
-        } else if ((long long)(gtimer() - t0) > a.ctl.timeout_ns || ld_acquire_s32(a.ctl.abort)) {
+        } else if ((++spins & 63) == 0 &&
+                   ((long long)(gtimer() - t0) > a.ctl.timeout_ns || ld_acquire_s32(a.ctl.abort))) {
+          // the bound and the abort flag are checked every 64 polls: an
+          // extra L2 round trip on every poll doubled the poll period
           raise_timeout(a.ctl);
           done = true;
         }
@@ -432,6 +440,13 @@ rf_status adjoint_ordered(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, 
     return RF_ERR_CUDA;
   // every warp that takes a ticket must be resident: a cooperative launch
   // guarantees it
+  // a small resident window: lanes that spin on unfinished children cost
+  // L2 bandwidth that the lanes at the front need; 2 CTAs of 8 warps per SM
+  // measured best on GB300 (5.98 ms vs 8.41 ms at the full occupancy of 4,
+  // 2048^2 workload; 4.83 ms with relaxed polling loads).  A lane-granular hand-out (free lanes taking new
+  // positions while others wait) measured slower (11.3 ms): it widens the
+  // window.
+  per_sm = per_sm < 2 ? per_sm : 2;
   void *args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void *)ordered_gather_kernel, dim3(per_sm * ctx->num_sms), dim3(256),
                                   args, 0, s) != cudaSuccess)
