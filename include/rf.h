@@ -288,6 +288,15 @@ rf_status rf_unet_conv3x3(rf_ctx *ctx, const uint16_t *x, int B, int H, int W,
                           int Cin, const uint16_t *w, const float *bias,
                           int Cout, int relu, uint16_t *y, float *y32,
                           void *stream);
+/* The same convolution on the fifth-generation tensor cores (tcgen05.mma,
+ * BF16 operands in shared memory, FP32 accumulator in tensor memory): same
+ * arguments, same result up to FP32 summation order.  A tensor-core wait
+ * that exceeds the context timeout sets RF_ERR_TIMEOUT in the context
+ * statistics. */
+rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, int H,
+                             int W, int Cin, const uint16_t *w,
+                             const float *bias, int Cout, int relu,
+                             uint16_t *y, float *y32, void *stream);
 /* dw [Cout][3][3][Cin] (FP32) += sum over pixels of dy (x) im2col(x): the
  * weight gradient; the caller zeroes dw. */
 rf_status rf_unet_conv3x3_wgrad(rf_ctx *ctx, const uint16_t *x,

@@ -1,0 +1,301 @@
+// rf_unet_tc.cu -- the warm-start network's 3x3 convolution on the fifth-
+// generation tensor cores: tcgen05.mma with BF16 operands in shared memory
+// and the FP32 accumulator in tensor memory (TMEM).
+//
+// Implicit GEMM per CTA: D[128 pixels][N out-channels] = sum over the 9 taps
+// and the input channels of A_tap[128][Cin] * B_tap[N][Cin]^T, where the 128
+// pixels are an 8 x 16 output tile and A_tap is the input patch shifted by
+// the tap.  Input channels are processed in chunks of CC (16, 32 or 64).
+//
+// Shared-memory operands use the no-swizzle K-major canonical layout: a
+// core matrix is 8 rows x 8 BF16 (16 bytes per row, 128 contiguous bytes).
+// * A: three copies of the 10 x 16 input patch, one per column tap kx
+//   (columns kx .. kx+15 of the 18-wide halo patch), stored
+//   [kx][c8][row 0..9][col 0..15][8 channels].  For tap (ky, kx) the
+//   matrix starts at row ky of copy kx; its 128 rows (8 rows x 16 columns
+//   of pixels) are 16 consecutive core matrices 128 bytes apart (stride
+//   byte offset 128, a patch row being 2 core matrices), and the second 8
+//   channels of an MMA's K = 16 sit one channel plane (10 x 16 x 16 B =
+//   2560 B) further (leading byte offset).
+// * B: the chunk's weights [tap][c8][n][8 channels]: N rows 16 bytes apart
+//   (stride byte offset 128 per 8 rows), next 8 channels one c8 plane
+//   (N x 16 B) further.
+// One thread issues the 9 x CC/16 MMAs of a chunk and commits them to an
+// mbarrier; all threads wait (bounded) before the chunk's buffers are
+// rewritten.  The epilogue reads the accumulator with tcgen05.ld (warp w
+// owns TMEM lanes 32w .. 32w+31 = pixels 32w ..), adds the bias, applies
+// ReLU and stores BF16 (and optionally FP32).
+#include <cuda_bf16.h>
+
+#include "rf_ctx.h"
+
+namespace rf {
+namespace tc {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kTH = 8, kTW = 16;  // output tile 8 x 16 = 128 pixels = MMA M
+constexpr int kPH = kTH + 2;      // patch rows
+constexpr int kThreads = 128;     // 4 warps: one per 32 TMEM lanes
+constexpr unsigned kPlaneBytes = kPH * kTW * 16;  // one 8-channel plane of a patch copy
+// Dynamic shared memory is at least this large, so that every address the
+// descriptors can form stays inside the CTA's allocation.
+constexpr size_t kMinSmem = 160 * 1024;
+
+__device__ __forceinline__ unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (PTX ISA, tcgen05 matrix descriptors):
+// start address >> 4 in bits 0-13, leading byte offset >> 4 in 16-29,
+// stride byte offset >> 4 in 32-45, descriptor version 1 in 46-47, base
+// offset 0, layout type 0 (no swizzle) in 61-63.
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor for kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28, dense, no negation.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N, int M) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(saddr(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, unsigned parity, long long timeout_ns) {
+  if (mbar_try_wait(m, parity)) return true;
+  const unsigned long long t0 = gtimer_ns();
+  while (!mbar_try_wait(m, parity))
+    if ((long long)(gtimer_ns() - t0) > timeout_ns) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *m) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(m))
+               : "memory");
+}
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+  const bf16 *x;      // [B][H][W][Cin]
+  const bf16 *w;      // [Cout][9][Cin]
+  const float *bias;  // [Cout] or null
+  bf16 *y;            // [B][H][W][Cout]
+  float *y32;         // optional FP32 copy
+  int B, H, W, Cin, Cout, relu, CC;
+  DevState *st;
+  long long timeout_ns;
+};
+
+__host__ __device__ inline size_t tc_smem_bytes(int CC, int N) {
+  const size_t a = (size_t)3 * (CC / 8) * kPlaneBytes, b = (size_t)9 * (CC / 8) * N * 16;
+  const size_t need = a + b + 16;  // + mbarrier and TMEM slot
+  return need > kMinSmem ? need : kMinSmem;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) conv3x3_tc_kernel(TcArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  constexpr unsigned kCols = N < 32 ? 32 : N;  // TMEM columns: a power of two >= 32
+  const int CC = a.CC, c8n = CC / 8;
+  const unsigned a_copy = (unsigned)c8n * kPlaneBytes;
+  bf16 *As = reinterpret_cast<bf16 *>(sm);
+  bf16 *Bs = reinterpret_cast<bf16 *>(sm + 3 * a_copy);
+  const unsigned b_bytes = 9u * c8n * N * 16;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 3 * a_copy + b_bytes);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  __shared__ int s_late;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_x = (a.W + kTW - 1) / kTW;
+  const int tx0 = (blockIdx.x % tiles_x) * kTW, ty0 = (blockIdx.x / tiles_x) * kTH;
+  const int n0 = blockIdx.y * N, b = blockIdx.z;
+  const int H = a.H, W = a.W, Cin = a.Cin, Cout = a.Cout;
+
+  if (warp == 0) tmem_alloc(tslot, kCols);
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+    s_late = 0;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = idesc_bf16(N, 128);
+
+  unsigned phase = 0;
+  for (int c0 = 0; c0 < Cin && !s_late; c0 += CC) {
+    // A: patch copies [kx][c8][row][col][8 ch] from x (zero outside the image)
+    const int na = 3 * c8n * kPH * kTW;
+    for (int f = tid; f < na; f += kThreads) {
+      const int col = f % kTW;
+      int r = f / kTW;
+      const int row = r % kPH;
+      r /= kPH;
+      const int c8 = r % c8n, kx = r / c8n;
+      const int gy = ty0 + row - 1, gx = tx0 + col + kx - 1;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+        v = *reinterpret_cast<const uint4 *>(a.x + (((long long)b * H + gy) * W + gx) * Cin + c0 + c8 * 8);
+      *reinterpret_cast<uint4 *>(As + ((size_t)((kx * c8n + c8) * kPH + row) * kTW + col) * 8) = v;
+    }
+    // B: weights [tap][c8][n][8 ch] of output channels n0 .. n0+N-1
+    const int nb = 9 * c8n * N;
+    for (int f = tid; f < nb; f += kThreads) {
+      const int n = f % N;
+      int r = f / N;
+      const int c8 = r % c8n, t = r / c8n;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (n0 + n < Cout) v = *reinterpret_cast<const uint4 *>(a.w + ((long long)(n0 + n) * 9 + t) * Cin + c0 + c8 * 8);
+      *reinterpret_cast<uint4 *>(Bs + ((size_t)(t * c8n + c8) * N + n) * 8) = v;
+    }
+    fence_proxy_async();  // the tensor cores read shared memory through the async proxy
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      const unsigned abase = saddr(As), bbase = saddr(Bs);
+      for (int t = 0; t < 9; ++t) {
+        const int ky = t / 3, kx = t % 3;
+        for (int ks = 0; ks < CC / 16; ++ks) {
+          const unsigned aaddr = abase + kx * a_copy + (2 * ks) * kPlaneBytes + ky * (kTW * 16);
+          const unsigned baddr = bbase + (unsigned)((t * c8n + 2 * ks) * N * 16);
+          mma_bf16(tmem, smem_desc(aaddr, kPlaneBytes, 128), smem_desc(baddr, N * 16, 128), idesc,
+                   (c0 > 0 || t > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(mbar);
+      // wait (bounded) for the chunk's MMAs: they read the buffers the next
+      // chunk rewrites, and the epilogue reads their result
+      if (!mbar_wait(mbar, phase, a.timeout_ns)) s_late = 1;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    fence_after();
+  }
+  if (s_late) {
+    // the chunk's MMAs did not report completion within the bound: record
+    // it, then wait once more (bounded) before the accumulator is freed
+    if (tid == 0) {
+      set_error(a.st, RF_ERR_TIMEOUT);
+      mbar_wait(mbar, phase ^ 1u, a.timeout_ns);
+    }
+    __syncthreads();
+  } else {
+    // epilogue: pixel m = 32 warp + lane of the tile, accumulator row m
+    const int m = warp * 32 + lane, gy = ty0 + m / kTW, gx = tx0 + m % kTW;
+    const bool in = gy < H && gx < W;
+    const long long obase = (((long long)b * H + gy) * W + gx) * Cout + n0;
+#pragma unroll
+    for (int cb = 0; cb < N; cb += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
+      if (in) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int co = n0 + cb + j;
+          if (co < Cout) {
+            float v = __uint_as_float(r[j]) + (a.bias ? a.bias[co] : 0.0f);
+            if (a.relu) v = fmaxf(v, 0.0f);
+            a.y[obase + cb + j] = __float2bfloat16(v);
+            if (a.y32) a.y32[obase + cb + j] = v;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+template <int N>
+rf_status launch(const TcArgs &a, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(a.CC, N);
+  if (cudaFuncSetAttribute(conv3x3_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return RF_ERR_CUDA;
+  const int tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH);
+  dim3 grid(tiles, (a.Cout + N - 1) / N, a.B);
+  conv3x3_tc_kernel<N><<<grid, kThreads, smem, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace tc
+}  // namespace rf
+
+using namespace rf;
+
+extern "C" rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, int H, int W, int Cin,
+                                        const uint16_t *w, const float *bias, int Cout, int relu, uint16_t *y,
+                                        float *y32, void *stream) {
+  if (!ctx || !x || !w || !y || B < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 || Cout < 16 || Cout % 16)
+    return RF_ERR_INVALID_ARG;
+  if (B > 65535) return RF_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  tc::TcArgs a;
+  a.x = reinterpret_cast<const tc::bf16 *>(x);
+  a.w = reinterpret_cast<const tc::bf16 *>(w);
+  a.bias = bias;
+  a.y = reinterpret_cast<tc::bf16 *>(y);
+  a.y32 = y32;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.Cin = Cin;
+  a.Cout = Cout;
+  a.relu = relu;
+  a.CC = (Cin % 64 == 0) ? 64 : (Cin % 32 == 0) ? 32 : 16;
+  a.st = ctx->state;
+  a.timeout_ns = ctx->timeout_ns;
+  if (Cout % 64 == 0) return tc::launch<64>(a, s);
+  if (Cout % 32 == 0) return tc::launch<32>(a, s);
+  return tc::launch<16>(a, s);
+}

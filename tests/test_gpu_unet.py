@@ -64,6 +64,42 @@ def test_conv3x3_forward_dgrad_wgrad(B, H, W, Cin, Cout, relu):
     assert rel(db.cpu().numpy(), dy.sum(axis=(0, 1, 2))) < 1e-5
 
 
+@pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(2, 13, 37, 32, 48, 1), (1, 8, 16, 16, 16, 0), (1, 24, 40, 96, 32, 1),
+                                               (1, 16, 32, 64, 64, 1), (2, 9, 20, 128, 64, 0), (1, 8, 16, 384, 128, 1)])
+def test_conv3x3_tcgen05_forward_and_dgrad(B, H, W, Cin, Cout, relu):
+    """The tcgen05 convolution (BF16 operands in shared memory, FP32
+    accumulator in tensor memory) against the FP64 reference, forward and
+    data gradient, and against the mma.sync kernel."""
+    rng = np.random.default_rng(B * 1000 + H * 10 + Cin)
+    ctx, lib, s = Context.get(0), L.load(), _stream()
+    x_t, x = bf16(rng.standard_normal((B, H, W, Cin)))
+    w_t, w = bf16(rng.standard_normal((Cout, 3, 3, Cin)) * 0.2)
+    bias = rng.standard_normal(Cout).astype(np.float32)
+    b_t = torch.from_numpy(bias).cuda()
+    y = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+    y32 = torch.empty((B, H, W, Cout), dtype=torch.float32, device="cuda")
+    L.check(lib.rf_unet_conv3x3_tc(ctx.handle, _ptr(x_t), B, H, W, Cin, _ptr(w_t), _ptr(b_t), Cout, relu, _ptr(y),
+                                   _ptr(y32), s), "conv_tc")
+    torch.cuda.synchronize()
+    assert ctx.stats()["status"] == 0
+    ref = U.conv3x3(x, w, bias, bool(relu))
+    assert rel(y32.cpu().numpy(), ref) < 1e-5
+    assert rel(y.float().cpu().numpy(), ref) < 1e-2
+    y32m = torch.empty_like(y32)
+    ym = torch.empty_like(y)
+    L.check(lib.rf_unet_conv3x3(ctx.handle, _ptr(x_t), B, H, W, Cin, _ptr(w_t), _ptr(b_t), Cout, relu, _ptr(ym),
+                                _ptr(y32m), s), "conv")
+    assert (y32 - y32m).abs().max().item() <= 1e-4 * max(1.0, y32m.abs().max().item())
+    dy_t, dy = bf16(rng.standard_normal((B, H, W, Cout)))
+    wt = torch.empty((Cin, 3, 3, Cout), dtype=torch.bfloat16, device="cuda")
+    L.check(lib.rf_unet_flip_weights(ctx.handle, _ptr(w_t), Cin, Cout, _ptr(wt), s), "flip")
+    dx = torch.empty((B, H, W, Cin), dtype=torch.bfloat16, device="cuda")
+    dx32 = torch.empty((B, H, W, Cin), dtype=torch.float32, device="cuda")
+    L.check(lib.rf_unet_conv3x3_tc(ctx.handle, _ptr(dy_t), B, H, W, Cout, _ptr(wt), None, Cin, 0, _ptr(dx),
+                                   _ptr(dx32), s), "dgrad_tc")
+    assert rel(dx32.cpu().numpy(), U.conv3x3_dgrad(dy, w)) < 1e-5
+
+
 def test_pool_upsample_concat_relu_mse():
     rng = np.random.default_rng(7)
     ctx, lib, s = Context.get(0), L.load(), _stream()
