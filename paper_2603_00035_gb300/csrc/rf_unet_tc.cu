@@ -5,7 +5,7 @@
 // Implicit GEMM per CTA: D[128 pixels][N out-channels] = sum over the 9 taps
 // and the input channels of A_tap[128][Cin] * B_tap[N][Cin]^T, where the 128
 // pixels are an 8 x 16 output tile and A_tap is the input patch shifted by
-// the tap.  Input channels are processed in chunks of CC (16, 32 or 64).
+// the tap.  Input channels are processed in chunks of CC (16 or 32).
 //
 // Shared-memory operands use the no-swizzle K-major canonical layout: a
 // core matrix is 8 rows x 8 BF16 (16 bytes per row, 128 contiguous bytes).
@@ -38,9 +38,6 @@ constexpr int kTH = 8, kTW = 16;  // output tile 8 x 16 = 128 pixels = MMA M
 constexpr int kPH = kTH + 2;      // patch rows
 constexpr int kThreads = 128;     // 4 warps: one per 32 TMEM lanes
 constexpr unsigned kPlaneBytes = kPH * kTW * 16;  // one 8-channel plane of a patch copy
-// Dynamic shared memory is at least this large, so that every address the
-// descriptors can form stays inside the CTA's allocation.
-constexpr size_t kMinSmem = 160 * 1024;
 
 __device__ __forceinline__ unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -134,12 +131,11 @@ struct TcArgs {
 
 __host__ __device__ inline size_t tc_smem_bytes(int CC, int N) {
   const size_t a = (size_t)3 * (CC / 8) * kPlaneBytes, b = (size_t)9 * (CC / 8) * N * 16;
-  const size_t need = a + b + 16;  // + mbarrier and TMEM slot
-  return need > kMinSmem ? need : kMinSmem;
+  return a + b + 16;  // + mbarrier and TMEM slot
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads, 1) conv3x3_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) conv3x3_tc_kernel(TcArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
   constexpr unsigned kCols = N < 32 ? 32 : N;  // TMEM columns: a power of two >= 32
   const int CC = a.CC, c8n = CC / 8;
@@ -235,16 +231,24 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_tc_kernel(TcArgs a) {
     for (int cb = 0; cb < N; cb += 16) {
       uint32_t r[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
-      if (in) {
+      if (in && n0 + cb < Cout) {  // Cout is a multiple of 16: all 16 columns are in range
+        float v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int co = n0 + cb + j;
-          if (co < Cout) {
-            float v = __uint_as_float(r[j]) + (a.bias ? a.bias[co] : 0.0f);
-            if (a.relu) v = fmaxf(v, 0.0f);
-            a.y[obase + cb + j] = __float2bfloat16(v);
-            if (a.y32) a.y32[obase + cb + j] = v;
-          }
+          v[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[n0 + cb + j] : 0.0f);
+          if (a.relu) v[j] = fmaxf(v[j], 0.0f);
+        }
+        uint4 pk[2];
+        __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.y + obase + cb);
+        dst[0] = pk[0];
+        dst[1] = pk[1];
+        if (a.y32) {
+          float4 *d32 = reinterpret_cast<float4 *>(a.y32 + obase + cb);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) d32[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
       }
     }
@@ -292,9 +296,12 @@ extern "C" rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, i
   a.Cin = Cin;
   a.Cout = Cout;
   a.relu = relu;
-  a.CC = (Cin % 64 == 0) ? 64 : (Cin % 32 == 0) ? 32 : 16;
+  // 32-channel chunks keep a CTA's buffers small enough for two CTAs per
+  // SM, so that one CTA's loads overlap the other's MMAs
+  a.CC = (Cin % 32 == 0) ? 32 : 16;
   a.st = ctx->state;
   a.timeout_ns = ctx->timeout_ns;
+  if (Cout % 128 == 0) return tc::launch<128>(a, s);
   if (Cout % 64 == 0) return tc::launch<64>(a, s);
   if (Cout % 32 == 0) return tc::launch<32>(a, s);
   return tc::launch<16>(a, s);
