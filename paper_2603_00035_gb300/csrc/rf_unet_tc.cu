@@ -25,7 +25,11 @@
 // rewritten.  The epilogue reads the accumulator with tcgen05.ld (warp w
 // owns TMEM lanes 32w .. 32w+31 = pixels 32w ..), adds the bias, applies
 // ReLU and stores BF16 (and optionally FP32).
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "rf_ctx.h"
 
@@ -258,6 +262,249 @@ __global__ void __launch_bounds__(kThreads, 2) conv3x3_tc_kernel(TcArgs a) {
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined form: the operand tiles arrive by tensor copies
+// (cp.async.bulk.tensor) into a ring of STAGES buffers, 16 input channels
+// per stage, while the tensor cores consume earlier stages.
+//  * warp 0 (producer): per stage, lane 0 arms the stage's "full" barrier
+//    with the stage's bytes, then 6 lanes copy the A planes (3 column taps
+//    x 2 channel planes, box 8 ch x 16 cols x 10 rows from the NHWC input,
+//    zero-filled outside the image) and 18 lanes the B planes (9 taps x 2
+//    channel planes, box 8 ch x N out-channels); it reuses a stage once
+//    the MMAs that read it have committed to its "empty" barrier;
+//  * warp 1, lane 0 (MMA issuer): waits for a stage, issues its 9 MMAs
+//    (one per tap, K = 16), commits them to the stage's empty barrier, and
+//    after the last stage commits to the "done" barrier;
+//  * all 4 warps: epilogue from TMEM as in conv3x3_tc_kernel.
+// Every wait is bounded by the context timeout; a timeout records
+// RF_ERR_TIMEOUT and the CTA drains what it issued before freeing TMEM.
+constexpr int kStages = 4;
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *m) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(saddr(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(m))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          saddr(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(saddr(m))
+      : "memory");
+}
+
+struct TmaArgs {
+  const float *bias;
+  bf16 *y;
+  float *y32;
+  int B, H, W, Cin, Cout, relu;
+  DevState *st;
+  long long timeout_ns;
+};
+
+__host__ __device__ constexpr unsigned stage_a_bytes() { return 3u * 2u * kPlaneBytes; }
+__host__ __device__ constexpr unsigned stage_b_bytes(int N) { return 9u * 2u * (unsigned)N * 16u; }
+__host__ __device__ constexpr size_t tma_smem_bytes(int N) {
+  return (size_t)kStages * (stage_a_bytes() + stage_b_bytes(N)) + (2 * kStages + 1) * 8 + 16;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv3x3_tma_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
+                       TmaArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  constexpr unsigned kCols = N < 32 ? 32 : N;
+  constexpr unsigned SA = stage_a_bytes(), SB = stage_b_bytes(N), SS = SA + SB;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + kStages * SS);
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  __shared__ int s_late;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_x = (a.W + kTW - 1) / kTW;
+  const int tx0 = (blockIdx.x % tiles_x) * kTW, ty0 = (blockIdx.x / tiles_x) * kTH;
+  const int n0 = blockIdx.y * N, b = blockIdx.z;
+  const int nchunks = a.Cin / 16;
+
+  if (warp == 0) tmem_alloc(tslot, kCols);
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+    s_late = 0;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  int issued = 0;  // producer: chunks whose copies were issued
+
+  if (warp == 0) {
+    for (int i = 0; i < nchunks; ++i) {
+      const int st = i % kStages;
+      const unsigned u = (unsigned)(i / kStages);
+      int ok = 1;
+      if (lane == 0 && i >= kStages) ok = mbar_wait(&empty[st], (u - 1u) & 1u, a.timeout_ns);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) s_late = 1;
+        break;
+      }
+      unsigned char *sa = sm + st * SS, *sb = sa + SA;
+      if (lane == 0) mbar_arrive_tx(&full[st], SA + SB);
+      __syncwarp();
+      const int c8_0 = i * 2;  // first 8-channel plane of this chunk
+      if (lane < 6) {
+        const int kx = lane >> 1, c8 = lane & 1;
+        tma_load_4d(sa + (kx * 2 + c8) * kPlaneBytes, &xmap, (c8_0 + c8) * 8, tx0 + kx - 1, ty0 - 1, b, &full[st]);
+      } else if (lane < 24) {
+        const int j = lane - 6, t = j >> 1, c8 = j & 1;
+        tma_load_3d(sb + (t * 2 + c8) * N * 16, &wmap, (c8_0 + c8) * 8, t, n0, &full[st]);
+      }
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(N, 128);
+    int i = 0;
+    for (; i < nchunks; ++i) {
+      const int st = i % kStages;
+      const unsigned u = (unsigned)(i / kStages);
+      if (!mbar_wait(&full[st], u & 1u, a.timeout_ns)) {
+        s_late = 1;
+        break;
+      }
+      fence_after();
+      const unsigned abase = saddr(sm + st * SS), bbase = abase + SA;
+      for (int t = 0; t < 9; ++t) {
+        const int ky = t / 3, kx = t % 3;
+        // A: copy kx = planes (kx, c8 0) and (kx, c8 1), 2560 B apart; row ky
+        const unsigned aaddr = abase + (kx * 2) * kPlaneBytes + ky * (kTW * 16);
+        const unsigned baddr = bbase + (unsigned)(t * 2 * N * 16);
+        mma_bf16(tmem, smem_desc(aaddr, kPlaneBytes, 128), smem_desc(baddr, N * 16, 128), idesc,
+                 (i > 0 || t > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[st]);
+    }
+    mma_commit(done);  // tracks every MMA issued above
+  }
+  // all warps: wait for the accumulator (bounded)
+  if (tid == 0 && !mbar_wait(done, 0u, a.timeout_ns)) s_late = 1;
+  __syncthreads();
+  if (s_late) {
+    if (tid == 0) {
+      set_error(a.st, RF_ERR_TIMEOUT);
+      // drain: the copies of every issued stage and the MMAs (bounded)
+      for (int st = 0; st < kStages; ++st) mbar_wait(&full[st], 0u, a.timeout_ns);
+      mbar_wait(done, 0u, a.timeout_ns);
+    }
+    __syncthreads();
+  } else {
+    fence_after();
+    const int m = warp * 32 + lane, gy = ty0 + m / kTW, gx = tx0 + m % kTW;
+    const bool in = gy < a.H && gx < a.W;
+    const long long obase = (((long long)b * a.H + gy) * a.W + gx) * a.Cout + n0;
+#pragma unroll
+    for (int cb = 0; cb < N; cb += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
+      if (in && n0 + cb < a.Cout) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          v[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[n0 + cb + j] : 0.0f);
+          if (a.relu) v[j] = fmaxf(v[j], 0.0f);
+        }
+        uint4 pk[2];
+        __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.y + obase + cb);
+        dst[0] = pk[0];
+        dst[1] = pk[1];
+        if (a.y32) {
+          float4 *d32 = reinterpret_cast<float4 *>(a.y32 + obase + cb);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) d32[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+      }
+    }
+  }
+  (void)issued;
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// Tensor maps.  x: dims (Cin, W, H, B) of the NHWC input, box (8, 16, 10, 1)
+// = one A plane [row][col][8 ch]; w: dims (Cin, 9, Cout) of the weights
+// [Cout][9][Cin], box (8, 1, N) = one B plane [n][8 ch].
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+template <int N>
+rf_status launch_tma(const TcArgs &t, cudaStream_t s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return RF_ERR_UNSUPPORTED;
+  alignas(64) CUtensorMap xmap, wmap;
+  const cuuint64_t xdim[4] = {(cuuint64_t)t.Cin, (cuuint64_t)t.W, (cuuint64_t)t.H, (cuuint64_t)t.B};
+  const cuuint64_t xstr[3] = {(cuuint64_t)t.Cin * 2, (cuuint64_t)t.W * t.Cin * 2, (cuuint64_t)t.H * t.W * t.Cin * 2};
+  const cuuint32_t xbox[4] = {8, kTW, kPH, 1};
+  const cuuint32_t one4[4] = {1, 1, 1, 1};
+  if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)t.x, xdim, xstr, xbox, one4,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return RF_ERR_UNSUPPORTED;
+  const cuuint64_t wdim[3] = {(cuuint64_t)t.Cin, 9, (cuuint64_t)t.Cout};
+  const cuuint64_t wstr[2] = {(cuuint64_t)t.Cin * 2, (cuuint64_t)9 * t.Cin * 2};
+  const cuuint32_t wbox[3] = {8, 1, (cuuint32_t)N};
+  const cuuint32_t one3[3] = {1, 1, 1};
+  if (enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)t.w, wdim, wstr, wbox, one3,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return RF_ERR_UNSUPPORTED;
+  TmaArgs a;
+  a.bias = t.bias;
+  a.y = t.y;
+  a.y32 = t.y32;
+  a.B = t.B;
+  a.H = t.H;
+  a.W = t.W;
+  a.Cin = t.Cin;
+  a.Cout = t.Cout;
+  a.relu = t.relu;
+  a.st = t.st;
+  a.timeout_ns = t.timeout_ns;
+  const size_t smem = tma_smem_bytes(N);
+  if (cudaFuncSetAttribute(conv3x3_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return RF_ERR_CUDA;
+  const int tiles = ((t.W + kTW - 1) / kTW) * ((t.H + kTH - 1) / kTH);
+  dim3 grid(tiles, (t.Cout + N - 1) / N, t.B);
+  conv3x3_tma_kernel<N><<<grid, kThreads, smem, s>>>(xmap, wmap, a);
+  return cuda_status(cudaGetLastError());
+}
+
 template <int N>
 rf_status launch(const TcArgs &a, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(a.CC, N);
@@ -301,6 +548,14 @@ extern "C" rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, i
   a.CC = (Cin % 32 == 0) ? 32 : 16;
   a.st = ctx->state;
   a.timeout_ns = ctx->timeout_ns;
+  // the pipelined tensor-copy kernel; the plain one if a tensor map cannot
+  // be encoded here
+  rf_status rs = RF_ERR_UNSUPPORTED;
+  if (Cout % 128 == 0) rs = tc::launch_tma<128>(a, s);
+  else if (Cout % 64 == 0) rs = tc::launch_tma<64>(a, s);
+  else if (Cout % 32 == 0) rs = tc::launch_tma<32>(a, s);
+  else rs = tc::launch_tma<16>(a, s);
+  if (rs != RF_ERR_UNSUPPORTED) return rs;
   if (Cout % 128 == 0) return tc::launch<128>(a, s);
   if (Cout % 64 == 0) return tc::launch<64>(a, s);
   if (Cout % 32 == 0) return tc::launch<32>(a, s);

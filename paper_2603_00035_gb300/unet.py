@@ -1,7 +1,7 @@
 """The learned warm start's network: a 4-level U-Net (32 base channels)
 whose every convolution, pooling, upsampling, concatenation, ReLU backward
 and loss runs in librf's kernels (rf_unet_*), BF16 activations with FP32
-accumulation.  PyTorch holds the tensors and runs Adam on the FP32 master
+accumulation; the wide convolutions run on the tcgen05 tensor cores.  PyTorch holds the tensors and runs Adam on the FP32 master
 weights.
 
 Layers (NHWC, channels padded to multiples of 16):
@@ -38,6 +38,15 @@ def layer_plan(cin=16, base=32, cout=16):
 
 def _chk(st, where):
     L.check(st, where)
+
+
+def conv3x3(lib, h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s):
+    """rf_unet_conv3x3 on the tcgen05 kernel (tensor-memory accumulator, tensor
+    copies) where it measured faster on GB300 -- 128 or more output channels
+    (288-361 vs 236-256 TFLOP/s) -- and on the mma.sync kernel for the narrow
+    layers (176-223 vs 57-192 TFLOP/s at 32-64 output channels)."""
+    fn = lib.rf_unet_conv3x3_tc if Cout % 128 == 0 else lib.rf_unet_conv3x3
+    return fn(h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s)
 
 
 class UNet:
@@ -128,8 +137,8 @@ class UNet:
                 y32 = None
                 if name == "out":
                     y32 = out32 = torch.empty((B_, H_, W_, co), dtype=torch.float32, device=self.dev)
-                _chk(lib.rf_unet_conv3x3(h, _ptr(cur), B_, H_, W_, ci, _ptr(self.Wbf[name]), _ptr(self.b[name]), co,
-                                         int(relu), _ptr(y), _ptr(y32), s), "conv3x3")
+                _chk(conv3x3(lib, h, _ptr(cur), B_, H_, W_, ci, _ptr(self.Wbf[name]), _ptr(self.b[name]), co,
+                             int(relu), _ptr(y), _ptr(y32), s), "conv3x3")
                 tape.append(("conv", name, cur, y, relu))
                 cur = y
         self._tape = tape
@@ -159,8 +168,8 @@ class UNet:
                     g = None  # no gradient needed for the network input
                     continue
                 dx = torch.empty((B_, H_, W_, ci), dtype=torch.bfloat16, device=self.dev)
-                _chk(lib.rf_unet_conv3x3(h, _ptr(g), B_, H_, W_, co, _ptr(self.Wflip[name]), None, ci, 0, _ptr(dx),
-                                         None, s), "dgrad")
+                _chk(conv3x3(lib, h, _ptr(g), B_, H_, W_, co, _ptr(self.Wflip[name]), None, ci, 0, _ptr(dx), None,
+                             s), "dgrad")
                 g = dx
             elif kind == "cat":
                 _, ca, sname = rec
