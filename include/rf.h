@@ -165,6 +165,66 @@ rf_status rf_project_backward(rf_ctx *ctx, const rf_grid *grid,
                               float eps, float delta, const float *dproj5,
                               float *draw5, void *stream);
 
+/* ---- the paper's own parameterisation (G, b) -----------------------------
+ * Paper: App. B "Feasibility Projections" and "Total Variation
+ * Regularization"; Eq. 8 (the regularised inverse problem).
+ * gb5: 5 planes (g11, g12, g22, b1, b2) -- the symmetric metric G and the
+ * drift b of the paper, [ny*nx] each, row-major.  The solver reads the
+ * factor form proj5 = (L11, L21, L22, wx, wy) with M = L L^T + eps I = G and
+ * w = -b (the drift-sign reading: the solver's cost is sqrt(v^T M v) + w.v).
+ */
+typedef struct rf_metric_params {
+  float lam_min; /* eigenvalue floor, eps < lam_min <= lam_max */
+  float lam_max; /* eigenvalue ceiling */
+  float b_max;   /* Euclidean clip of the drift, > 0 (INFINITY: none) */
+  float delta;   /* feasibility margin: |b|_{G^-1} <= 1 - delta, 0<delta<1 */
+  float eps;     /* the solver's eps (M = L L^T + eps I), >= 0 */
+} rf_metric_params;
+
+/* Projection layer, per node in App. B's order:
+ *   1. eigenvalues lambda_pm = ((g11+g22) +- sqrt((g11-g22)^2 + 4 g12^2))/2
+ *      clamped to [lam_min, lam_max], G rebuilt on the principal axes
+ *      (angle atan2(2 g12, g11 - g22)/2);
+ *   2. |b|_2 clipped to b_max, then b scaled by (1-delta)/n when
+ *      n = |b|_{G^-1} = sqrt((b1^2 g22 - 2 b1 b2 g12 + b2^2 g11)/det G)
+ *      (projected G) exceeds 1 - delta;
+ *   3. L = chol(G - eps I), w = -b.
+ * gbp5 (nullable): projected (g11, g12, g22, b1, b2), may alias gb5 (the
+ * in-place projection of projected gradient descent).  proj5 (nullable):
+ * the solver's factor form.  Non-finite input sets RF_ERR_NONFINITE_INPUT in
+ * the device status word. */
+rf_status rf_metric_project(rf_ctx *ctx, const rf_grid *grid, const float *gb5,
+                            const rf_metric_params *prm, float *gbp5,
+                            float *proj5, void *stream);
+
+/* Backward of rf_metric_project (recomputed from gb5, nothing stored):
+ * dgb5 = dL/d(gb5) of a loss that reads proj5 (gradient dproj5, nullable)
+ * and/or gbp5 (gradient dgbp5, nullable; e.g. a regulariser).  The clamp is
+ * differentiated by the Daleckii-Krein formula (derivative 1 inside the
+ * closed interval, 0 outside; divided difference across the two
+ * eigenvalues); g12's gradient is with respect to the one parameter that
+ * enters G twice.  dgb5 may alias dgbp5. */
+rf_status rf_metric_project_backward(rf_ctx *ctx, const rf_grid *grid,
+                                     const float *gb5,
+                                     const rf_metric_params *prm,
+                                     const float *dproj5, const float *dgbp5,
+                                     float *dgb5, void *stream);
+
+/* Total-variation regularisers of App. B with forward differences (zero in
+ * the last column/row, no grid spacing):
+ *   R(b) = sum_ij sqrt(sum_d (D_d b1)^2 + (D_d b2)^2),
+ *   R(G) = sum_ij sqrt(sum_d (D_d a11)^2 + 2 (D_d a12)^2 + (D_d a22)^2)
+ * with a = G (RF_TV_FROBENIUS) or a = log G (RF_TV_LOG_EUCLIDEAN, closed
+ * form on the eigenvectors; G must be SPD, else RF_ERR_NONFINITE_INPUT in
+ * the device status word).  value2 (device, nullable): [R(G), R(b)]
+ * (unweighted; R(G) = 0 for RF_TV_NONE), deterministic order.  grad5
+ * (device, nullable): += w_metric dR(G)/d(g11,g12,g22), w_drift
+ * dR(b)/d(b1,b2); the subgradient is 0 where a node's norm is 0. */
+enum rf_tv_metric { RF_TV_NONE = 0, RF_TV_FROBENIUS = 1, RF_TV_LOG_EUCLIDEAN = 2 };
+rf_status rf_tv(rf_ctx *ctx, const rf_grid *grid, const float *gb5,
+                int metric_mode, float w_metric, float w_drift, float *value2,
+                float *grad5, void *stream);
+
 /* ---- a2-a5: forward solve -------------------------------------------------
  * Paper: Sec. 3.2 (Eqs. 2-3), App. A "Forward Solve Pseudocode" (Alg. 1).
  * proj5: projected 5-plane fields; src: [ny*nx] uint8 source mask (non-zero

@@ -38,6 +38,14 @@ class Opts(ctypes.Structure):
                 ("variant", ctypes.c_int32)]
 
 
+class MetricParams(ctypes.Structure):
+    _fields_ = [("lam_min", ctypes.c_float), ("lam_max", ctypes.c_float), ("b_max", ctypes.c_float),
+                ("delta", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+RF_TV_NONE, RF_TV_FROBENIUS, RF_TV_LOG_EUCLIDEAN = 0, 1, 2
+
+
 class Record(ctypes.Structure):
     _fields_ = [("id", ctypes.c_void_p), ("w1", ctypes.c_void_p), ("dT", ctypes.c_void_p)]
 
@@ -89,6 +97,9 @@ def load(path: str = LIB_PATH):
                            ctypes.POINTER(Record), P, P, P, P],
         "rf_sweep_forward_static": [ctypes.POINTER(Grid), P, F, P, ctypes.POINTER(Opts), P,
                                     ctypes.POINTER(Stats), P],
+        "rf_metric_project": [P, ctypes.POINTER(Grid), P, ctypes.POINTER(MetricParams), P, P, P],
+        "rf_metric_project_backward": [P, ctypes.POINTER(Grid), P, ctypes.POINTER(MetricParams), P, P, P, P],
+        "rf_tv": [P, ctypes.POINTER(Grid), P, I, F, F, P, P, P],
     }
     I64 = ctypes.c_int64
     sig.update({

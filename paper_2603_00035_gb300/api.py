@@ -122,6 +122,70 @@ def rf_project_backward(raw5, clip, eps, delta, dproj5, draw5=None, ctx=None, st
     return draw5
 
 
+def metric_params(lam_min=1e-2, lam_max=1e2, b_max=None, delta=0.05, eps=1e-6):
+    """rf_metric_params of App. B's projection: eigenvalues clamped to
+    [lam_min, lam_max], |b|_2 <= b_max (default (1-delta) sqrt(lam_max), the
+    largest Euclidean norm a feasible drift can have), |b|_{G^-1} <= 1-delta;
+    eps is the solver's (M = L L^T + eps I)."""
+    if b_max is None:
+        b_max = (1.0 - delta) * lam_max ** 0.5
+    return L.MetricParams(float(lam_min), float(lam_max), float(b_max), float(delta), float(eps))
+
+
+def rf_metric_project(gb5, prm, gbp5=None, proj5=None, want_gbp=True, want_proj=True, ctx=None, stream=None):
+    """App. B projection of the paper's (g11, g12, g22, b1, b2): returns
+    (gbp5 projected, proj5 the solver's factor form); either may be skipped.
+    gbp5 may be gb5 itself (in-place projection)."""
+    _check_cuda(gb5, torch.float32, name="gb5")
+    _, ny, nx = gb5.shape
+    ctx = ctx or Context.get(gb5.device)
+    if want_gbp and gbp5 is None:
+        gbp5 = torch.empty_like(gb5)
+    if want_proj and proj5 is None:
+        proj5 = torch.empty_like(gb5)
+    g = _grid(ny, nx, 1.0)
+    L.check(L.load().rf_metric_project(ctx.handle, ctypes.byref(g), _ptr(gb5), ctypes.byref(prm),
+                                       _ptr(gbp5) if want_gbp else None, _ptr(proj5) if want_proj else None,
+                                       _stream(stream)), "rf_metric_project")
+    return (gbp5 if want_gbp else None), (proj5 if want_proj else None)
+
+
+def rf_metric_project_backward(gb5, prm, dproj5=None, dgbp5=None, dgb5=None, ctx=None, stream=None):
+    """Gradient wrt the raw gb5 from gradients wrt proj5 and/or gbp5."""
+    _check_cuda(gb5, torch.float32, name="gb5")
+    for t, nm in ((dproj5, "dproj5"), (dgbp5, "dgbp5")):
+        if t is not None:
+            _check_cuda(t, torch.float32, gb5.shape, name=nm)
+    _, ny, nx = gb5.shape
+    ctx = ctx or Context.get(gb5.device)
+    dgb5 = dgb5 if dgb5 is not None else torch.empty_like(gb5)
+    g = _grid(ny, nx, 1.0)
+    L.check(L.load().rf_metric_project_backward(ctx.handle, ctypes.byref(g), _ptr(gb5), ctypes.byref(prm),
+                                                _ptr(dproj5), _ptr(dgbp5), _ptr(dgb5), _stream(stream)),
+            "rf_metric_project_backward")
+    return dgb5
+
+
+TV_METRIC = {"none": L.RF_TV_NONE, "frobenius": L.RF_TV_FROBENIUS, "log_euclidean": L.RF_TV_LOG_EUCLIDEAN}
+
+
+def rf_tv(gb5, metric="frobenius", w_metric=1.0, w_drift=1.0, grad5=None, value=True, ctx=None, stream=None):
+    """App. B total variation of (G, b): returns (values [R(G), R(b)] as a
+    CUDA float32 tensor or None, grad5) with grad5 += w_metric dR(G) +
+    w_drift dR(b) when grad5 is given."""
+    _check_cuda(gb5, torch.float32, name="gb5")
+    if grad5 is not None:
+        _check_cuda(grad5, torch.float32, gb5.shape, name="grad5")
+    _, ny, nx = gb5.shape
+    ctx = ctx or Context.get(gb5.device)
+    mode = TV_METRIC[metric] if isinstance(metric, str) else int(metric)
+    val = torch.empty(2, dtype=torch.float32, device=gb5.device) if value else None
+    g = _grid(ny, nx, 1.0)
+    L.check(L.load().rf_tv(ctx.handle, ctypes.byref(g), _ptr(gb5), mode, float(w_metric), float(w_drift),
+                           _ptr(val), _ptr(grad5), _stream(stream)), "rf_tv")
+    return val, grad5
+
+
 SWEEP_VARIANTS = {"auto": L.RF_SWEEP_AUTO, "tiled1": L.RF_SWEEP_TILED1, "streamed": L.RF_SWEEP_STREAMED,
                   "tiled4": L.RF_SWEEP_TILED4}
 

@@ -48,3 +48,75 @@ class RFSolve(torch.autograd.Function):
 def rf_solve(raw5, src, h, eps=1e-6, delta=0.05, algo="ordered", opts=None):
     """Differentiable arrival times T(raw5) (see RFSolve)."""
     return RFSolve.apply(raw5, src, h, eps, delta, algo, opts)
+
+
+# ---- the paper's own parameterisation (App. B) ---------------------------------
+
+class MetricProject(torch.autograd.Function):
+    """(gbp5, proj5) = MetricProject.apply(gb5, prm): App. B projection of
+    (g11, g12, g22, b1, b2) -- eigenvalue clamp, drift clip and G^-1-norm
+    rescale -- and the solver's factor form.  Backward recomputes from gb5."""
+
+    @staticmethod
+    def forward(ctx, gb5, prm):
+        gb5 = gb5.contiguous()
+        gbp5, proj5 = api.rf_metric_project(gb5, prm)
+        ctx.save_for_backward(gb5)
+        ctx.prm = prm
+        return gbp5, proj5
+
+    @staticmethod
+    def backward(ctx, dgbp5, dproj5):
+        (gb5,) = ctx.saved_tensors
+        dgbp5 = dgbp5.contiguous() if dgbp5 is not None else None
+        dproj5 = dproj5.contiguous() if dproj5 is not None else None
+        return api.rf_metric_project_backward(gb5, ctx.prm, dproj5=dproj5, dgbp5=dgbp5), None
+
+
+class SweepSolve(torch.autograd.Function):
+    """T = SweepSolve.apply(proj5, src, h, eps, algo, opts): the solve of an
+    already-feasible factor-form field (no projection), differentiated by the
+    stencil-record adjoint (Alg. 2)."""
+
+    @staticmethod
+    def forward(ctx, proj5, src, h, eps=1e-6, algo="ordered", opts=None):
+        proj5 = proj5.contiguous()
+        T, rec = api.rf_sweep_forward(proj5, eps, src, h, opts=opts)
+        ctx.save_for_backward(src, T, rec.id, rec.w1, rec.dT)
+        ctx.algo = algo
+        return T
+
+    @staticmethod
+    def backward(ctx, gT):
+        src, T, rid, rw1, rdT = ctx.saved_tensors
+        g = torch.nan_to_num(gT.contiguous().to(torch.float32), nan=0.0, posinf=0.0, neginf=0.0)
+        gproj, _ = api.rf_adjoint(src, T, api.Record(rid, rw1, rdT), g, algo=ctx.algo, lam=False)
+        return gproj, None, None, None, None, None
+
+
+class TotalVariation(torch.autograd.Function):
+    """w_metric R(G) + w_drift R(b) of App. B (metric: "frobenius",
+    "log_euclidean" or "none") as a 0-d tensor."""
+
+    @staticmethod
+    def forward(ctx, gb5, metric="frobenius", w_metric=1.0, w_drift=1.0):
+        gb5 = gb5.contiguous()
+        val, _ = api.rf_tv(gb5, metric)
+        ctx.save_for_backward(gb5)
+        ctx.cfg = (metric, w_metric, w_drift)
+        return w_metric * val[0] + w_drift * val[1]
+
+    @staticmethod
+    def backward(ctx, gout):
+        (gb5,) = ctx.saved_tensors
+        metric, wm, wd = ctx.cfg
+        grad = torch.zeros_like(gb5)
+        api.rf_tv(gb5, metric, wm, wd, grad5=grad, value=False)
+        return grad * gout, None, None, None
+
+
+def metric_solve(gb5, src, h, prm, algo="ordered", opts=None):
+    """Differentiable T of the paper's raw (g11, g12, g22, b1, b2) fields:
+    App. B projection, then the solve.  Returns (T, gbp5)."""
+    gbp5, proj5 = MetricProject.apply(gb5, prm)
+    return SweepSolve.apply(proj5, src, h, prm.eps, algo, opts), gbp5

@@ -38,6 +38,7 @@ extern "C" rf_status rf_ctx_destroy(rf_ctx *c) {
   cudaFree(c->scratch);
   cudaFree(c->adj_state);
   cudaFree(c->recbuf);
+  cudaFree(c->tvbuf);
   delete c;
   return RF_OK;
 }

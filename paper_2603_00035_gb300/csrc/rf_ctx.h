@@ -32,6 +32,8 @@ struct rf_ctx {
   unsigned adj_epoch = 0;  // launch counter tagging adj_state words
   float4 *recbuf = nullptr;  // streamed sweep: node records, both orientations
   size_t recbuf_cap = 0;
+  float *tvbuf = nullptr;  // total variation: per-block partial sums
+  size_t tvbuf_cap = 0;
 };
 
 namespace rf {

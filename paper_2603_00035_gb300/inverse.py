@@ -1,15 +1,18 @@
-"""Inverse metric problem (Sec. 4, Eq. 8) driven through RFSolve.
+"""Inverse metric problem (Sec. 4, Eq. 8) driven through the solver.
+
+run_inverse: the factor-form parameterisation,
 
     min_theta  1/2 sum_{i in obs} (T_i(theta) - T_hat_i)^2
 
 over theta = (L11, L21, L22, wx, wy) on every node, with Adam at the
 paper's step sizes (1e-2 for the metric, 5e-3 for the drift; Sec. 4).  The
-projection inside RFSolve keeps M SPD and the drift feasible.  The TV
-regularisers of Eq. 8 are not part of this driver.
+projection inside RFSolve keeps M SPD and the drift feasible.  The
+observations come from a ground-truth solve of a known field; the initial
+guess is M = I, w = 0 (the paper does not state one).
 
-The observations come from a ground-truth solve of a known field; the
-initial guess is M = I, w = 0 (the paper does not state one).  Returns the
-loss history and the relative recovery error of M and w.
+run_inverse_paper / paper_experiments: the paper's own parameterisation
+(G, b) with the App. B projections and TV regularisers, and its 80 x 80
+synthetic recoveries (isotropic, drift, multi-source, TV ablation).
 """
 from __future__ import annotations
 
@@ -18,7 +21,7 @@ import time
 import torch
 
 from . import api
-from .autograd import rf_solve
+from .autograd import TotalVariation, metric_solve, rf_solve
 
 
 def metric_from_raw(raw5, eps):
@@ -70,6 +73,139 @@ def run_inverse(raw_true, src, obs, h, steps=200, eps=1e-6, delta=0.05, lr_metri
                 seconds=elapsed, steps=steps)
 
 
+def run_inverse_paper(gb_true, sources, obs, h, mode="iso", steps=300, init=1.5, tv_weight=1e-3,
+                      tv_metric="frobenius", prm=None, lr_metric=1e-2, lr_drift=5e-3, clip=1.0, algo="ordered",
+                      opts=None, noise=0.0, seed=0):
+    """The paper's synthetic inverse experiments (Eq. 8; App. "Inverse
+    Problem Experiments") in its own parameterisation (G, b):
+
+        min 1/2 sum_s sum_{i in obs_s} (T_i^s - T^_i^s)^2 + w (R(G) + R(b))
+
+    with T^s the solve of source mask s on the true fields.  Each iteration
+    evaluates the data term through the App. B projection, the solves and
+    the stencil-record adjoint, adds the TV gradient, takes an Adam step
+    (learning rates 1e-2 for G and 5e-3 for b, gradient norm clipped, cosine
+    decay) and projects the parameters back onto the feasible set (projected
+    gradient descent).
+
+    mode "iso": G = g I with g free (b fixed to the truth); "drift": b free
+    (G fixed to the truth); "full": all five fields free.  gb_true: float32
+    CUDA (5, ny, nx); sources: list of uint8 (ny, nx) masks; obs: list of
+    uint8 masks (one per source); noise: Gaussian noise added to the observed
+    times, as a fraction of their standard deviation.  Returns the loss
+    history, relative errors (of the fields, and of the drift's mean) and
+    timing."""
+    dev = gb_true.device
+    prm = prm or api.metric_params()
+    ny, nx = gb_true.shape[1:]
+    with torch.no_grad():
+        _, proj_true = api.rf_metric_project(gb_true, prm, want_gbp=False)
+        targets = [api.rf_sweep_forward(proj_true, prm.eps, s, h, record=False)[0] for s in sources]
+    obs_f = [o.to(torch.float32) for o in obs]
+    if noise > 0:
+        gen = torch.Generator(device="cpu").manual_seed(int(seed))
+        targets = [t + noise * float(t[o.bool()].std()) * torch.randn(t.shape, generator=gen).to(dev)
+                   for o, t in zip(obs, targets)]
+    targets = [torch.where(o.bool(), t, torch.zeros_like(t)) for o, t in zip(obs, targets)]
+    z = torch.zeros((ny, nx), dtype=torch.float32, device=dev)
+    if mode == "iso":
+        params = [torch.nn.Parameter(torch.full((ny, nx), float(init), device=dev))]
+        groups = [{"params": params, "lr": lr_metric}]
+        assemble = lambda: torch.stack([params[0], z, params[0], gb_true[3], gb_true[4]])
+    elif mode == "drift":
+        params = [torch.nn.Parameter(torch.full((2, ny, nx), float(init), device=dev))]
+        groups = [{"params": params, "lr": lr_drift}]
+        assemble = lambda: torch.cat([gb_true[:3], params[0]])
+    elif mode == "full":
+        g0 = torch.stack([torch.full((ny, nx), float(init), device=dev), z, torch.full((ny, nx), float(init),
+                                                                                    device=dev)])
+        params = [torch.nn.Parameter(g0), torch.nn.Parameter(torch.zeros((2, ny, nx), device=dev))]
+        groups = [{"params": [params[0]], "lr": lr_metric}, {"params": [params[1]], "lr": lr_drift}]
+        assemble = lambda: torch.cat([params[0], params[1]])
+    else:
+        raise ValueError(mode)
+    opt = torch.optim.Adam(groups)
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, steps, eta_min=0.1 * lr_drift)
+    hist = []
+    t0 = time.perf_counter()
+    for it in range(steps):
+        opt.zero_grad(set_to_none=True)
+        gb = assemble()
+        loss = torch.zeros((), device=dev)
+        gbp = None
+        for s, o, tgt in zip(sources, obs_f, targets):
+            T, gbp = metric_solve(gb, s, h, prm, algo, opts)
+            d = torch.where(o.bool(), T - tgt, torch.zeros_like(T))
+            loss = loss + 0.5 * (d * d * o).sum()
+        if tv_weight > 0:
+            loss = loss + TotalVariation.apply(gbp, tv_metric, tv_weight, tv_weight)
+        loss.backward()
+        if clip:
+            torch.nn.utils.clip_grad_norm_(params, clip)
+        opt.step()
+        sched.step()
+        with torch.no_grad():  # projection onto the feasible set
+            gbp_new, _ = api.rf_metric_project(assemble().contiguous(), prm, want_proj=False)
+            if mode == "iso":
+                params[0].copy_(gbp_new[0])
+            elif mode == "drift":
+                params[0].copy_(gbp_new[3:])
+            else:
+                params[0].copy_(gbp_new[:3])
+                params[1].copy_(gbp_new[3:])
+        if it % 10 == 0 or it == steps - 1:
+            hist.append((it, float(loss.detach())))
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    with torch.no_grad():
+        gb = assemble()
+        rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        out = dict(mode=mode, steps=steps, sources=len(sources), observations=int(sum(int(o.sum()) for o in obs)),
+                   tv_weight=tv_weight, final_loss=hist[-1][1], loss_history=hist, seconds=elapsed,
+                   ms_per_iteration=1e3 * elapsed / steps)
+        if mode in ("iso", "full"):
+            out["rel_err_metric"] = rel(gb[:3], gb_true[:3])
+        if mode in ("drift", "full"):
+            out["rel_err_b1"] = rel(gb[3], gb_true[3])
+            out["rel_err_b2"] = rel(gb[4], gb_true[4])
+            for c in (3, 4):
+                m_true = float(gb_true[c].mean())
+                out[f"rel_err_b{c - 2}_mean"] = abs(float(gb[c].mean()) - m_true) / abs(m_true)
+    return out
+
+
+def paper_experiments(steps=300, seed=0, device="cuda"):
+    """The synthetic recoveries of the paper's inverse-problem section on an
+    80 x 80 grid (h = 1/79): isotropic piecewise metric (g = 1 | 2) with
+    full and 7 % observations, constant drift (0.15, 0.08) under G = I,
+    multi-source recovery with 1, 2, 3, 5 sources at 7 % each, and the TV
+    weight ablation on full observations with 2 % noise.  Yields one result
+    dict per run."""
+    import numpy as np
+
+    import rf_inputs as R
+
+    n, h = 80, 1.0 / 79
+    dev = torch.device(device)
+    t = lambda a: torch.from_numpy(a).to(dev)
+    iso = t(R.piecewise_isotropic(n))
+    centre = [t(R.point_sources(n, n, [(n // 2, n // 2)]))]
+    full = [t(np.ones((n, n), np.uint8))]
+    sparse = lambda k: [t(R.observation_mask(n, n, 0.07, seed + 17 * i)) for i in range(k)]
+    yield dict(run="isotropic_full_obs", **run_inverse_paper(iso, centre, full, h, "iso", steps))
+    yield dict(run="isotropic_7pct_obs", **run_inverse_paper(iso, centre, sparse(1), h, "iso", steps))
+    drift = t(R.constant_gb(n, (1.0, 0.0, 1.0), (0.15, 0.08)))
+    for w in (1e-3, 1e-2):
+        yield dict(run=f"drift_full_obs_tv{w:g}", **run_inverse_paper(drift, centre, full, h, "drift", steps, init=0.0,
+                                                                     tv_weight=w))
+    for k in (1, 2, 3, 5):
+        srcs = [t(m) for m in (R.random_sources(n, n, 1, seed + 101 * i, margin=8) for i in range(k))]
+        yield dict(run=f"multisource_{k}", **run_inverse_paper(iso, srcs, sparse(k), h, "iso", steps))
+    for w in (0.0, 1e-4, 1e-3, 1e-2, 1e-1):
+        yield dict(run=f"tv_ablation_{w:g}", **run_inverse_paper(iso, centre, full, h, "iso", steps, tv_weight=w,
+                                                                 noise=0.02, seed=seed))
+
+
 def main():
     import argparse
     import json
@@ -85,7 +221,14 @@ def main():
     p.add_argument("--obs", type=float, default=0.005)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--algo", default="ordered")
+    p.add_argument("--paper", action="store_true",
+                   help="run the paper's 80x80 synthetic recoveries in its (G, b) parameterisation")
     a = p.parse_args()
+    if a.paper:
+        for r in paper_experiments(steps=a.steps if a.steps != 200 else 300, seed=a.seed):
+            r.pop("loss_history")
+            print(json.dumps(r), flush=True)
+        return
     c = R.config_inverse(n=a.n, seed=a.seed)
     dev = torch.device("cuda")
     raw_true = torch.from_numpy(c["raw"]).to(dev)

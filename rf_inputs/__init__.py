@@ -93,6 +93,41 @@ def randers_fields(ny, nx, h, K, seed, eps=1e-6, omega="unit", omega_scale=0.3, 
     return np.ascontiguousarray(out)
 
 
+def gb_fields(ny, nx, h, K, seed, drift_max=1.5):
+    """Raw fields in the paper's own parameterisation, float32 (5, ny, nx) =
+    (g11, g12, g22, b1, b2): G = R(theta) diag(a^2, b^2) R(theta)^T with
+    a, b in [0.5, 2] as above (eigenvalues in [0.25, 4]), and a drift of
+    direction 2 pi f_phi and magnitude drift_max * f_r -- the kind of
+    unconstrained output a network produces, for the projection to act on."""
+    th = math.pi * fourier_field(ny, nx, h, K, rng_for(seed, FIELD_THETA))
+    a = 0.5 * 4.0 ** fourier_field(ny, nx, h, K, rng_for(seed, FIELD_A))
+    b = 0.5 * 4.0 ** fourier_field(ny, nx, h, K, rng_for(seed, FIELD_B))
+    ct, st = np.cos(th), np.sin(th)
+    g11 = a * a * ct * ct + b * b * st * st
+    g12 = (a * a - b * b) * ct * st
+    g22 = a * a * st * st + b * b * ct * ct
+    ph = 2.0 * math.pi * fourier_field(ny, nx, h, K, rng_for(seed, FIELD_PHI))
+    r = drift_max * fourier_field(ny, nx, h, K, rng_for(seed, FIELD_R))
+    out = np.stack([g11, g12, g22, r * np.cos(ph), r * np.sin(ph)]).astype(np.float32)
+    return np.ascontiguousarray(out)
+
+
+def piecewise_isotropic(n=80, g_left=1.0, g_right=2.0):
+    """The paper's isotropic inverse-experiment truth (App. "Inverse Problem
+    Experiments"): G = g I on an n x n grid, g = g_left for columns j < n/2
+    and g_right for the rest; zero drift.  float32 (5, n, n) in (g11, g12,
+    g22, b1, b2)."""
+    g = np.where(np.arange(n)[None, :] < n // 2, g_left, g_right) * np.ones((n, 1))
+    z = np.zeros((n, n))
+    return np.ascontiguousarray(np.stack([g, z, g, z, z]).astype(np.float32))
+
+
+def constant_gb(n, g=(1.0, 0.0, 1.0), b=(0.0, 0.0)):
+    """Constant (g11, g12, g22, b1, b2) on an n x n grid, float32."""
+    vals = list(g) + list(b)
+    return np.ascontiguousarray(np.stack([np.full((n, n), float(v)) for v in vals]).astype(np.float32))
+
+
 def constant_fields(ny, nx, M, w, eps=0.0):
     """Constant metric M (2x2 SPD) and drift w, as raw float32 (5, ny, nx)."""
     M = np.asarray(M, dtype=np.float64)
