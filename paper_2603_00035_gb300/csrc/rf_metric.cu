@@ -28,14 +28,15 @@ struct Eig2 {
 
 __device__ __forceinline__ Eig2 eig2(float g11, float g12, float g22) {
   Eig2 e;
-  const float d = g11 - g22;
-  e.r = hypotf(d, 2.0f * g12);
+  const float d = g11 - g22, t = 2.0f * g12;
+  e.r = sqrtf(fmaf(d, d, t * t));
   const float tr = g11 + g22;
   e.lp = 0.5f * (tr + e.r);
   e.lm = 0.5f * (tr - e.r);
   const bool iso = !(e.r > 0.0f);
-  e.c2 = iso ? 1.0f : d / e.r;
-  e.s2 = iso ? 0.0f : 2.0f * g12 / e.r;
+  const float ir = iso ? 0.0f : __frcp_rn(e.r);
+  e.c2 = iso ? 1.0f : d * ir;
+  e.s2 = t * ir;
   return e;
 }
 
@@ -108,6 +109,39 @@ __device__ __forceinline__ ProjNode proj_node(float g11, float g12, float g22, f
   return P;
 }
 
+// V consecutive nodes of one plane (V = 4: one 16-byte load or store).
+// Plain (coherent) loads: the projection may run in place.
+template <int V>
+struct Vec {
+  float v[V];
+};
+
+template <int V>
+__device__ __forceinline__ Vec<V> ldv(const float *p) {
+  Vec<V> r;
+  if constexpr (V == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    r.v[0] = t.x;
+    r.v[1] = t.y;
+    r.v[2] = t.z;
+    r.v[3] = t.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) r.v[k] = p[k];
+  }
+  return r;
+}
+
+template <int V>
+__device__ __forceinline__ void stv(float *p, const Vec<V> &r) {
+  if constexpr (V == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) p[k] = r.v[k];
+  }
+}
+
 struct MetricArgs {
   long long n;
   const float *gb;   // 5 planes
@@ -117,28 +151,43 @@ struct MetricArgs {
   DevState *st;
 };
 
+// V nodes per thread and iteration (V = 4 when n and every plane base are
+// 16-byte aligned): 5 x V in flight per thread keeps enough bytes in flight
+// for HBM at 8 warps per SM-quarter.
+template <int V>
 __global__ void __launch_bounds__(256) metric_project_kernel(MetricArgs a) {
-  const long long n = a.n;
+  const long long n = a.n, units = n / V;
   bool bad = false;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const float g11 = __ldg(a.gb + p), g12 = __ldg(a.gb + n + p), g22 = __ldg(a.gb + 2 * n + p),
-                b1 = __ldg(a.gb + 3 * n + p), b2 = __ldg(a.gb + 4 * n + p);
-    bad |= !(isfinite(g11) && isfinite(g12) && isfinite(g22) && isfinite(b1) && isfinite(b2));
-    const ProjNode P = proj_node(g11, g12, g22, b1, b2, a.m);
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
+       u += (long long)gridDim.x * blockDim.x) {
+    const long long p = u * V;
+    Vec<V> in[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) in[c] = ldv<V>(a.gb + c * n + p);
+    Vec<V> o[5], l[5];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const float g11 = in[0].v[k], g12 = in[1].v[k], g22 = in[2].v[k], b1 = in[3].v[k], b2 = in[4].v[k];
+      bad |= !(isfinite(g11) && isfinite(g12) && isfinite(g22) && isfinite(b1) && isfinite(b2));
+      const ProjNode P = proj_node(g11, g12, g22, b1, b2, a.m);
+      o[0].v[k] = P.o11;
+      o[1].v[k] = P.o12;
+      o[2].v[k] = P.o22;
+      o[3].v[k] = P.q1;
+      o[4].v[k] = P.q2;
+      l[0].v[k] = P.l11;
+      l[1].v[k] = P.l21;
+      l[2].v[k] = P.l22;
+      l[3].v[k] = -P.q1;
+      l[4].v[k] = -P.q2;
+    }
     if (a.gbp) {
-      a.gbp[p] = P.o11;
-      a.gbp[n + p] = P.o12;
-      a.gbp[2 * n + p] = P.o22;
-      a.gbp[3 * n + p] = P.q1;
-      a.gbp[4 * n + p] = P.q2;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) stv<V>(a.gbp + c * n + p, o[c]);
     }
     if (a.proj) {
-      a.proj[p] = P.l11;
-      a.proj[n + p] = P.l21;
-      a.proj[2 * n + p] = P.l22;
-      a.proj[3 * n + p] = -P.q1;
-      a.proj[4 * n + p] = -P.q2;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) stv<V>(a.proj + c * n + p, l[c]);
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_error(a.st, RF_ERR_NONFINITE_INPUT);
@@ -153,68 +202,98 @@ struct MetricBwdArgs {
   rf_metric_params m;
 };
 
+// backward of one node from its raw inputs and the two incoming gradients
+__device__ __forceinline__ void project_backward_node(const float in[5], float dl[5], const float dq[5],
+                                                      bool has_dl, bool has_dq, const rf_metric_params &m,
+                                                      float out[5]) {
+  const ProjNode P = proj_node(in[0], in[1], in[2], in[3], in[4], m);
+  const float c = 1.0f - m.delta;
+  float d11 = 0.f, d12 = 0.f, d22 = 0.f, db1 = 0.f, db2 = 0.f;
+  if (has_dl) {
+    // L = chol(G - eps I), w = -b, in reverse
+    d22 = dl[2] / (2.0f * P.l22);
+    const float dl21b = dl[1] - dl[2] * P.l21 / P.l22;
+    d12 = dl21b / P.l11;
+    d11 = (dl[0] - dl21b * P.l21 / P.l11) / (2.0f * P.l11);
+    db1 = -dl[3];
+    db2 = -dl[4];
+  }
+  if (has_dq) {
+    d11 += dq[0];
+    d12 += dq[1];
+    d22 += dq[2];
+    db1 += dq[3];
+    db2 += dq[4];
+  }
+  // drift rescale q = c e / n(e, G): into e and into the projected G
+  float de1 = db1, de2 = db2;
+  if (P.clip_n) {
+    const float bg = db1 * P.e1 + db2 * P.e2;
+    const float inv = 1.0f / P.n, in2 = inv * inv;
+    de1 = c * inv * (db1 - P.p1 * bg * in2);
+    de2 = c * inv * (db2 - P.p2 * bg * in2);
+    const float k = 0.5f * c * bg * in2 * inv;
+    d11 += k * P.p1 * P.p1;
+    d12 += 2.0f * k * P.p1 * P.p2;
+    d22 += k * P.p2 * P.p2;
+  }
+  // Euclidean clip e = b b_max/|b|
+  if (P.clip_e) {
+    const float ib = 1.0f / P.bn;
+    const float be = (in[3] * de1 + in[4] * de2) * ib * ib;
+    de1 = m.b_max * ib * (de1 - in[3] * be);
+    de2 = m.b_max * ib * (de2 - in[4] * be);
+  }
+  // eigenvalue clamp (Daleckii-Krein): f' = 1 inside [lam_min, lam_max]
+  const float Fp = (P.e.lp >= m.lam_min && P.e.lp <= m.lam_max) ? 1.0f : 0.0f;
+  const float Fm = (P.e.lm >= m.lam_min && P.e.lm <= m.lam_max) ? 1.0f : 0.0f;
+  const float F12 = P.e.r > 0.0f ? (P.mp - P.mm) / P.e.r : Fp;
+  dk_adjoint(P.e, Fp, F12, Fm, d11, d12, d22);
+  out[0] = d11;
+  out[1] = d12;
+  out[2] = d22;
+  out[3] = de1;
+  out[4] = de2;
+}
+
+template <int V>
 __global__ void __launch_bounds__(256) metric_project_backward_kernel(MetricBwdArgs a) {
-  const long long n = a.n;
-  const float c = 1.0f - a.m.delta;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const ProjNode P = proj_node(__ldg(a.gb + p), __ldg(a.gb + n + p), __ldg(a.gb + 2 * n + p),
-                                 __ldg(a.gb + 3 * n + p), __ldg(a.gb + 4 * n + p), a.m);
-    float d11 = 0.f, d12 = 0.f, d22 = 0.f, db1 = 0.f, db2 = 0.f;
-    if (a.dproj) {
-      // L = chol(G - eps I), w = -b, in reverse
-      const float dl11 = a.dproj[p], dl21 = a.dproj[n + p], dl22 = a.dproj[2 * n + p];
-      d22 = dl22 / (2.0f * P.l22);
-      const float dl21b = dl21 - dl22 * P.l21 / P.l22;
-      d12 = dl21b / P.l11;
-      d11 = (dl11 - dl21b * P.l21 / P.l11) / (2.0f * P.l11);
-      db1 = -a.dproj[3 * n + p];
-      db2 = -a.dproj[4 * n + p];
+  const long long n = a.n, units = n / V;
+  const bool has_dl = a.dproj != nullptr, has_dq = a.dgbp != nullptr;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
+       u += (long long)gridDim.x * blockDim.x) {
+    const long long p = u * V;
+    Vec<V> in[5], dl[5], dq[5], out[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      in[c] = ldv<V>(a.gb + c * n + p);
+      if (has_dl) dl[c] = ldv<V>(a.dproj + c * n + p);
+      if (has_dq) dq[c] = ldv<V>(a.dgbp + c * n + p);
     }
-    if (a.dgbp) {
-      d11 += a.dgbp[p];
-      d12 += a.dgbp[n + p];
-      d22 += a.dgbp[2 * n + p];
-      db1 += a.dgbp[3 * n + p];
-      db2 += a.dgbp[4 * n + p];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      float i5[5], l5[5], q5[5], o5[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        i5[c] = in[c].v[k];
+        l5[c] = has_dl ? dl[c].v[k] : 0.0f;
+        q5[c] = has_dq ? dq[c].v[k] : 0.0f;
+      }
+      project_backward_node(i5, l5, q5, has_dl, has_dq, a.m, o5);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) out[c].v[k] = o5[c];
     }
-    // drift rescale q = c e / n(e, G): into e and into the projected G
-    float de1 = db1, de2 = db2;
-    if (P.clip_n) {
-      const float bg = db1 * P.e1 + db2 * P.e2;
-      const float in = 1.0f / P.n, in2 = in * in;
-      de1 = c * in * (db1 - P.p1 * bg * in2);
-      de2 = c * in * (db2 - P.p2 * bg * in2);
-      const float k = 0.5f * c * bg * in2 * in;
-      d11 += k * P.p1 * P.p1;
-      d12 += 2.0f * k * P.p1 * P.p2;
-      d22 += k * P.p2 * P.p2;
-    }
-    // Euclidean clip e = b b_max/|b|
-    const float b1 = __ldg(a.gb + 3 * n + p), b2 = __ldg(a.gb + 4 * n + p);
-    if (P.clip_e) {
-      const float ib = 1.0f / P.bn;
-      const float be = (b1 * de1 + b2 * de2) * ib * ib;
-      de1 = a.m.b_max * ib * (de1 - b1 * be);
-      de2 = a.m.b_max * ib * (de2 - b2 * be);
-    }
-    // eigenvalue clamp (Daleckii-Krein): f' = 1 inside [lam_min, lam_max]
-    const float Fp = (P.e.lp >= a.m.lam_min && P.e.lp <= a.m.lam_max) ? 1.0f : 0.0f;
-    const float Fm = (P.e.lm >= a.m.lam_min && P.e.lm <= a.m.lam_max) ? 1.0f : 0.0f;
-    const float F12 = P.e.r > 0.0f ? (P.mp - P.mm) / P.e.r : Fp;
-    dk_adjoint(P.e, Fp, F12, Fm, d11, d12, d22);
-    a.dgb[p] = d11;
-    a.dgb[n + p] = d12;
-    a.dgb[2 * n + p] = d22;
-    a.dgb[3 * n + p] = de1;
-    a.dgb[4 * n + p] = de2;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) stv<V>(a.dgb + c * n + p, out[c]);
   }
 }
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 // ---------------------------------------------------------------------------
 // total variation
 // ---------------------------------------------------------------------------
-constexpr int kTvX = 32, kTvY = 8;          // nodes per tile
+constexpr int kTvX = 32, kTvY = 8;          // nodes per tile (one thread each)
 constexpr int kTvFX = kTvX + 2, kTvFY = kTvY + 2;  // staged field: one halo each side
 constexpr int kTvUX = kTvX + 1, kTvUY = kTvY + 1;  // unit differences: left/top halo
 
@@ -228,13 +307,14 @@ struct TvArgs {
   DevState *st;
 };
 
-// log G on the eigenvectors (G SPD): components of U diag(log lp, log lm) U^T
+// log G on the eigenvectors (G SPD): components of U diag(log lp, log lm) U^T;
+// e and hd = (log lp - log lm)/2 are returned for the backward's factors
 __device__ __forceinline__ bool logm2(float g11, float g12, float g22, float &l11, float &l12,
-                                      float &l22) {
-  const Eig2 e = eig2(g11, g12, g22);
+                                      float &l22, Eig2 &e, float &hd) {
+  e = eig2(g11, g12, g22);
   if (!(e.lm > 0.0f) || !isfinite(e.lp)) return false;
   const float ll = logf(e.lm);
-  const float hd = 0.5f * log1pf(e.r / e.lm);  // (log lp - log lm)/2, no cancellation
+  hd = 0.5f * log1pf(e.r / e.lm);  // (log lp - log lm)/2 without cancellation
   const float hs = ll + hd;
   l11 = fmaf(hd, e.c2, hs);
   l22 = fmaf(-hd, e.c2, hs);
@@ -243,12 +323,15 @@ __device__ __forceinline__ bool logm2(float g11, float g12, float g22, float &l1
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kTvX * kTvY) tv_kernel(TvArgs a) {
+__global__ void __launch_bounds__(kTvX * kTvY, 8) tv_kernel(TvArgs a) {
   constexpr int NC = MODE == RF_TV_NONE ? 2 : 5;  // staged components
   constexpr int C0 = MODE == RF_TV_NONE ? 3 : 0;  // first plane staged
   __shared__ float f[NC][kTvFY][kTvFX];
   __shared__ float ux[NC][kTvUY][kTvUX], uy[NC][kTvUY][kTvUX];
   __shared__ float red[2][kTvX * kTvY / 32];
+  // Log-Euclidean: the Daleckii-Krein factors of the tile's own nodes
+  // (cos 2theta, sin 2theta, 1/lp, (log lp - log lm)/(lp - lm), 1/lm)
+  __shared__ float dk[MODE == RF_TV_LOG_EUCLIDEAN ? 5 : 1][kTvY][kTvX];
   const int x0 = blockIdx.x * kTvX, y0 = blockIdx.y * kTvY;
   const int nx = a.nx, ny = a.ny;
   const long long n = (long long)nx * ny;
@@ -266,14 +349,24 @@ __global__ void __launch_bounds__(kTvX * kTvY) tv_kernel(TvArgs a) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) v[c] = __ldg(a.gb + (C0 + c) * n + p);
       if constexpr (MODE == RF_TV_LOG_EUCLIDEAN) {
-        float l11, l12, l22;
-        if (!logm2(v[0], v[1], v[2], l11, l12, l22)) {
+        float l11, l12, l22, hd;
+        Eig2 e;
+        const bool ok = logm2(v[0], v[1], v[2], l11, l12, l22, e, hd);
+        if (!ok) {
           bad = true;
           l11 = l12 = l22 = 0.0f;
         }
         v[0] = l11;
         v[1] = l12;
         v[2] = l22;
+        if (fy >= 1 && fy <= kTvY && fx >= 1 && fx <= kTvX) {
+          const int oy = fy - 1, ox = fx - 1;
+          dk[0][oy][ox] = e.c2;
+          dk[1][oy][ox] = e.s2;
+          dk[2][oy][ox] = ok ? 1.0f / e.lp : 0.0f;
+          dk[3][oy][ox] = ok ? (e.r > 0.0f ? 2.0f * hd / e.r : 1.0f / e.lp) : 0.0f;
+          dk[4][oy][ox] = ok ? 1.0f / e.lm : 0.0f;
+        }
       }
     }
 #pragma unroll
@@ -361,14 +454,11 @@ __global__ void __launch_bounds__(kTvX * kTvY) tv_kernel(TvArgs a) {
   }
   if constexpr (MODE == RF_TV_LOG_EUCLIDEAN) {
     // back through log G: F_ii = 1/lambda_i, F_12 = (log lp - log lm)/(lp - lm)
-    const float g11 = __ldg(a.gb + p), g12 = __ldg(a.gb + n + p), g22 = __ldg(a.gb + 2 * n + p);
-    const Eig2 e = eig2(g11, g12, g22);
-    if (e.lm > 0.0f) {
-      const float F12 = e.r > 0.0f ? log1pf(e.r / e.lm) / e.r : 1.0f / e.lp;
-      dk_adjoint(e, 1.0f / e.lp, F12, 1.0f / e.lm, g[0], g[1], g[2]);
-    } else {
-      g[0] = g[1] = g[2] = 0.0f;
-    }
+    // (a non-SPD node has all factors 0 and contributes nothing)
+    Eig2 e;
+    e.c2 = dk[0][ty][tx];
+    e.s2 = dk[1][ty][tx];
+    dk_adjoint(e, dk[2][ty][tx], dk[3][ty][tx], dk[4][ty][tx], g[0], g[1], g[2]);
   }
   if constexpr (MODE != RF_TV_NONE) {
 #pragma unroll
@@ -432,7 +522,11 @@ extern "C" rf_status rf_metric_project(rf_ctx *ctx, const rf_grid *grid, const f
   a.proj = proj5;
   a.m = *prm;
   a.st = ctx->state;
-  metric_project_kernel<<<blocks_for(a.n, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+  const bool vec = a.n % 4 == 0 && aligned16(gb5) && (!gbp5 || aligned16(gbp5)) && (!proj5 || aligned16(proj5));
+  if (vec)
+    metric_project_kernel<4><<<blocks_for(a.n / 4, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+  else
+    metric_project_kernel<1><<<blocks_for(a.n, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -450,7 +544,12 @@ extern "C" rf_status rf_metric_project_backward(rf_ctx *ctx, const rf_grid *grid
   a.dgbp = dgbp5;
   a.dgb = dgb5;
   a.m = *prm;
-  metric_project_backward_kernel<<<blocks_for(a.n, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+  const bool vec = a.n % 4 == 0 && aligned16(gb5) && aligned16(dgb5) && (!dproj5 || aligned16(dproj5)) &&
+                   (!dgbp5 || aligned16(dgbp5));
+  if (vec)
+    metric_project_backward_kernel<4><<<blocks_for(a.n / 4, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+  else
+    metric_project_backward_kernel<1><<<blocks_for(a.n, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 

@@ -195,7 +195,7 @@ def paper_experiments(steps=300, seed=0, device="cuda"):
     yield dict(run="isotropic_full_obs", **run_inverse_paper(iso, centre, full, h, "iso", steps))
     yield dict(run="isotropic_7pct_obs", **run_inverse_paper(iso, centre, sparse(1), h, "iso", steps))
     drift = t(R.constant_gb(n, (1.0, 0.0, 1.0), (0.15, 0.08)))
-    for w in (1e-3, 1e-2):
+    for w in (1e-3, 1e-2, 1e-1):
         yield dict(run=f"drift_full_obs_tv{w:g}", **run_inverse_paper(drift, centre, full, h, "drift", steps, init=0.0,
                                                                      tv_weight=w))
     for k in (1, 2, 3, 5):
