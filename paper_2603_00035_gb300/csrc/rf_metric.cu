@@ -152,10 +152,11 @@ struct MetricArgs {
 };
 
 // V nodes per thread and iteration (V = 4 when n and every plane base are
-// 16-byte aligned): 5 x V in flight per thread keeps enough bytes in flight
-// for HBM at 8 warps per SM-quarter.
+// 16-byte aligned): 5 x 16 B in flight per thread keeps enough bytes in
+// flight for HBM at 2-3 CTAs per SM; the grid is exactly the
+// resident CTAs, striding over the nodes.
 template <int V>
-__global__ void __launch_bounds__(256) metric_project_kernel(MetricArgs a) {
+__global__ void __launch_bounds__(256, 3) metric_project_kernel(MetricArgs a) {
   const long long n = a.n, units = n / V;
   bool bad = false;
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
@@ -257,7 +258,7 @@ __device__ __forceinline__ void project_backward_node(const float in[5], float d
 }
 
 template <int V>
-__global__ void __launch_bounds__(256) metric_project_backward_kernel(MetricBwdArgs a) {
+__global__ void __launch_bounds__(256, 2) metric_project_backward_kernel(MetricBwdArgs a) {
   const long long n = a.n, units = n / V;
   const bool has_dl = a.dproj != nullptr, has_dq = a.dgbp != nullptr;
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
@@ -289,6 +290,15 @@ __global__ void __launch_bounds__(256) metric_project_backward_kernel(MetricBwdA
 }
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+// grid-stride grid of exactly the resident CTAs (no partial last wave)
+template <class K>
+inline int resident_grid(K kernel, const rf_ctx *ctx, long long units) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return blocks_for(units, 256, ctx->num_sms * per_sm);
+}
 
 // ---------------------------------------------------------------------------
 // total variation
@@ -524,9 +534,9 @@ extern "C" rf_status rf_metric_project(rf_ctx *ctx, const rf_grid *grid, const f
   a.st = ctx->state;
   const bool vec = a.n % 4 == 0 && aligned16(gb5) && (!gbp5 || aligned16(gbp5)) && (!proj5 || aligned16(proj5));
   if (vec)
-    metric_project_kernel<4><<<blocks_for(a.n / 4, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+    metric_project_kernel<4><<<resident_grid(metric_project_kernel<4>, ctx, a.n / 4), 256, 0, s>>>(a);
   else
-    metric_project_kernel<1><<<blocks_for(a.n, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+    metric_project_kernel<1><<<resident_grid(metric_project_kernel<1>, ctx, a.n), 256, 0, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -547,9 +557,11 @@ extern "C" rf_status rf_metric_project_backward(rf_ctx *ctx, const rf_grid *grid
   const bool vec = a.n % 4 == 0 && aligned16(gb5) && aligned16(dgb5) && (!dproj5 || aligned16(dproj5)) &&
                    (!dgbp5 || aligned16(dgbp5));
   if (vec)
-    metric_project_backward_kernel<4><<<blocks_for(a.n / 4, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+    metric_project_backward_kernel<4><<<resident_grid(metric_project_backward_kernel<4>, ctx, a.n / 4), 256, 0,
+                                         s>>>(a);
   else
-    metric_project_backward_kernel<1><<<blocks_for(a.n, 256, ctx->num_sms * 8), 256, 0, s>>>(a);
+    metric_project_backward_kernel<1><<<resident_grid(metric_project_backward_kernel<1>, ctx, a.n), 256, 0,
+                                         s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
