@@ -276,16 +276,20 @@ struct OrderedArgs {
 };
 
 // Polling load: the child's multiplier and the epoch tag sit in one 64-bit
-// word written by one release store, so a relaxed (single-copy atomic)
-// load that sees the tag sees the value; unlike an acquire load it does
-// not hold back the loads of the other children.
+// word written by one store, so a relaxed (single-copy atomic) load that
+// sees the tag sees the value; unlike an acquire load it does not hold back
+// the loads of the other children.
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// Publishing store: a parent reads nothing of its child but this one 64-bit
+// word (multiplier and epoch tag together), so single-copy atomicity is all
+// the hand-over needs -- no release fence, which would first wait for the
+// thread's earlier gradient stores to reach L2.
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
@@ -303,6 +307,8 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
     unsigned cmask = 0;  // children among the 8 neighbours
     float cw[8];
     float gsum = 0.0f;
+    float dTp[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // partials, loaded before the wait
+    bool act = false;
     int pi = 0, pj = 0;
     if (!done) {
       p = a.order[pos];
@@ -311,10 +317,13 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
       const float tp = a.T[p];
       if (!(tp < kInf)) {
         // unreached: no residual, no children
-        st_release_u64(&a.state[p], tag);
+        st_relaxed_u64(&a.state[p], tag);
         done = true;
       } else {
         gsum = a.g[p];
+        act = a.id[p] != 0 && !a.src[p];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) dTp[c] = act ? a.dT[c * n + p] : 0.0f;
       }
     }
 #pragma unroll
@@ -343,10 +352,9 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
           }
         }
         if (ready) {
-          st_release_u64(&a.state[p], tag | __float_as_uint(acc));
-          const bool act = a.id[p] != 0 && !a.src[p];
+          st_relaxed_u64(&a.state[p], tag | __float_as_uint(acc));
 #pragma unroll
-          for (int c = 0; c < 5; ++c) a.grad[c * n + p] = act ? acc * a.dT[c * n + p] : 0.0f;
+          for (int c = 0; c < 5; ++c) a.grad[c * n + p] = act ? acc * dTp[c] : 0.0f;
           if (a.lam_out) a.lam_out[p] = acc;
           done = true;
         } else if ((++spins & 63) == 0 &&
@@ -439,14 +447,11 @@ rf_status adjoint_ordered(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, 
       per_sm < 1)
     return RF_ERR_CUDA;
   // every warp that takes a ticket must be resident: a cooperative launch
-  // guarantees it
-  // a small resident window: lanes that spin on unfinished children cost
-  // L2 bandwidth that the lanes at the front need; 2 CTAs of 8 warps per SM
-  // measured best on GB300 (5.98 ms vs 8.41 ms at the full occupancy of 4,
-  // 2048^2 workload; 4.83 ms with relaxed polling loads).  A lane-granular hand-out (free lanes taking new
-  // positions while others wait) measured slower (11.3 ms): it widens the
-  // window.
-  per_sm = per_sm < 2 ? per_sm : 2;
+  // guarantees it.  Full occupancy: with fence-free publishing the gather
+  // measured 2.72 / 2.50 / 2.45 / 2.45 ms at 1 / 2 / 3 / 4 CTAs per SM
+  // (2048^2 workload); with release stores a small window had been best
+  // (4.83 ms at 2 CTAs, 8.41 ms at 4).  A lane-granular hand-out (free
+  // lanes taking new positions while others wait) measured slower.
   void *args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void *)ordered_gather_kernel, dim3(per_sm * ctx->num_sms), dim3(256),
                                   args, 0, s) != cudaSuccess)
