@@ -195,6 +195,7 @@ def run_ours(args):
     import rf_inputs as R
     from paper_2603_00035_gb300 import api
     from paper_2603_00035_gb300 import build as B
+    from paper_2603_00035_gb300 import replicas
 
     rank, world, local = dist_info()
     if world > 1:
@@ -305,16 +306,12 @@ def run_ours(args):
                 e2e_ms += e0.elapsed_time(e1)
         h2d = h_raw.numel() * 4 + h_src.numel() + h_g.numel() * 4
         d2h = h_T.numel() * 4 + h_graw.numel() * 4
-        e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        e2e_rate, _ = replicas.job_rate(args.steps, e2e_ms, dev)
+        e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # max over ranks of the timed region
-    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t_local.item())
+    # whole job: the grids all ranks solved over the slowest rank's time
+    value, total_ms = replicas.job_rate(args.steps, total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
 
     phase_ms = phase / args.steps
     names = ["project", "sweep_forward", "record", "adjoint", "project_backward"]
@@ -378,11 +375,18 @@ def run_batch(args):
 
     from paper_2603_00035_gb300 import api
     from paper_2603_00035_gb300 import build as B
+    from paper_2603_00035_gb300 import replicas
 
+    rank, world, local = dist_info()
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
     B.build()
-    torch.cuda.set_device(0)
-    grids = batch_grids(args.grids)
-    nodes = sum(g["src"].size for g in grids)
+    torch.cuda.set_device(local)
+    all_grids = batch_grids(args.grids)
+    # independent grids shard with no data exchange: each rank solves its own
+    # size-balanced subset
+    grids = [all_grids[i] for i in replicas.shard([g["src"].size for g in all_grids], rank, world)]
+    nodes = sum(g["src"].size for g in all_grids)
     bs = api.BatchSolver(grids)
     bs.run()
     torch.cuda.synchronize()
@@ -390,12 +394,14 @@ def run_batch(args):
     for _ in range(args.warmup):
         bs.run()
     torch.cuda.synchronize()
-    st = api.Context.get(0).stats()
+    st = api.Context.get(local).stats()
     if st["status"] != 0 or int(bs.gstat[:, 0].abs().sum()) != 0:
         raise RuntimeError(f"batch status {st}, per-grid {bs.gstat[:, 0].tolist()}")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(local)
     sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0.record()
     for _ in range(args.steps):
@@ -403,10 +409,11 @@ def run_batch(args):
     e1.record()
     torch.cuda.synchronize()
     sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    rate, total = replicas.job_rate(len(grids) * args.steps, e0.elapsed_time(e1), torch.device("cuda", local))
+    ms = total / args.steps
     sweeps = bs.gstat[:, 1].double().mean().item()
     # the plain form: one grid after another through the single-grid entry points
-    dev = torch.device("cuda")
+    dev = torch.device("cuda", local)
     per = []
     for g in grids:
         raw = torch.from_numpy(g["raw"]).to(dev)
@@ -428,20 +435,24 @@ def run_batch(args):
     plain()
     e1.record()
     torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
+    plain_rate, plain_ms = replicas.job_rate(len(grids), e0.elapsed_time(e1), dev)
     line = {"metric": f"forward+adjoint solves/s, batch of {len(grids)} grids (sides 64..1024)",
-            "value": len(grids) / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "value": rate, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched forward+adjoint, {len(grids)} grids, long side U{{64..1024}}, "
                                    "half square / half 2:1, 1-8 sources, one persistent launch in a CUDA graph",
                        "nodes": int(nodes), "mean_sweeps": sweeps,
                        "l2": "working set > L2 (%.0f MB of fields)" % (nodes * 20 / 1e6)},
-            "plain_form": {"value": len(grids) / (plain_ms / 1e3), "unit": UNIT, "ms_per_batch": plain_ms,
+            "plain_form": {"value": plain_rate, "unit": UNIT, "ms_per_batch": plain_ms,
                            "how": "rf_project, rf_sweep_forward, rf_adjoint(ordered), rf_project_backward per grid"},
             "gpu_launches": 3 * args.steps,
             "clocks": sampler.summary()}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
 
 
 def run_appb(args):
