@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "forward+adjoint solves/s at 2048x2048"
 UNIT = "solves/s"
 ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-update
+# DRAM bytes (read + write) of one launch of the streamed sweep at 2048^2, (band, block) = (32, 32), from one
+# ncu capture (profiles/sweep_stream_kernel_2048_traffic.md); the record stream is most of it
+SWEEP_TRAFFIC_2048 = 6300210944 + 251966720
 # kernels of ours per step: project, init, source check, sweep, record, project backward, plus the
 # adjoint's own kernels (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not counted);
 # the streamed forward variant adds its node-record kernel
@@ -329,8 +332,12 @@ def run_ours(args):
     else:
         bytes_per_launch = 60 * n * n
     achieved = bytes_per_launch / (phase_ms[dom] / 1e3) / 1e9
+    traffic = None
+    if names[dom] == "sweep_forward" and n == 2048 and tile["variant"] in (0, STREAMED) and \
+            (tile["band"], tile["block"]) == (32, 32):
+        traffic = SWEEP_TRAFFIC_2048
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None}
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
