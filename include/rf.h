@@ -225,6 +225,25 @@ rf_status rf_tv(rf_ctx *ctx, const rf_grid *grid, const float *gb5,
                 int metric_mode, float w_metric, float w_drift, float *value2,
                 float *grad5, void *stream);
 
+/* ---- covariate encoder head (Sec. 5 "Encoder Architecture") -------------
+ * The global pathway gives each grid a baseline (G0, b0), the
+ * fully-convolutional pathway per-node residuals; they combine as
+ * G = G0 + alpha G_local, b = b0 + alpha b_local.
+ * local: FP32 NHWC [B][H][W][C] (channels 0..4 = residuals of g11, g12,
+ * g22, b1, b2; C >= 5); base: FP32 [B][Cb] (channels 0..4 = G0, b0;
+ * Cb >= 5); gb: FP32 out, per grid five planes of H*W nodes, grids back to
+ * back (gb[(b*5 + c)*H*W + p]) -- each grid's gb5 for rf_metric_project. */
+rf_status rf_encoder_combine(rf_ctx *ctx, const float *local, int B, int H,
+                             int W, int C, const float *base, int Cb,
+                             float alpha, float *gb, void *stream);
+/* Adjoint: dlocal (BF16 NHWC [B][H][W][C]) = alpha dgb on channels 0..4,
+ * 0 on the rest; dbase (BF16 [B][Cb]) = dgb summed over each grid's nodes
+ * (fixed-order reduction) on channels 0..4, 0 on the rest. */
+rf_status rf_encoder_combine_backward(rf_ctx *ctx, const float *dgb, int B,
+                                      int H, int W, int C, int Cb, float alpha,
+                                      uint16_t *dlocal, uint16_t *dbase,
+                                      void *stream);
+
 /* ---- a2-a5: forward solve -------------------------------------------------
  * Paper: Sec. 3.2 (Eqs. 2-3), App. A "Forward Solve Pseudocode" (Alg. 1).
  * proj5: projected 5-plane fields; src: [ny*nx] uint8 source mask (non-zero

@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
         "rf_metric_project": [P, ctypes.POINTER(Grid), P, ctypes.POINTER(MetricParams), P, P, P],
         "rf_metric_project_backward": [P, ctypes.POINTER(Grid), P, ctypes.POINTER(MetricParams), P, P, P, P],
         "rf_tv": [P, ctypes.POINTER(Grid), P, I, F, F, P, P, P],
+        "rf_encoder_combine": [P, P, I, I, I, I, P, I, F, P, P],
+        "rf_encoder_combine_backward": [P, P, I, I, I, I, I, F, P, P, P],
     }
     I64 = ctypes.c_int64
     sig.update({

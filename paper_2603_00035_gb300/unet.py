@@ -50,10 +50,12 @@ def conv3x3(lib, h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s):
 
 
 class UNet:
-    def __init__(self, cin=16, base=32, cout=16, device="cuda", seed=0, ctx=None):
+    def __init__(self, cin=16, base=32, cout=16, device="cuda", seed=0, ctx=None, plan=None):
+        """plan: a layer list in layer_plan's format (the last convolution
+        named "out"); default the 4-level U-Net."""
         self.dev = torch.device(device)
         self.ctx = ctx or Context.get(self.dev)
-        self.plan = layer_plan(cin, base, cout)
+        self.plan = plan if plan is not None else layer_plan(cin, base, cout)
         self.cin, self.cout = cin, cout
         g = torch.Generator(device="cpu").manual_seed(seed)
         self.W, self.b = {}, {}
@@ -208,7 +210,10 @@ class UNet:
         count = float(mask.sum().item()) if mask is not None else float(npix)
         loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
         dout = torch.empty((B_, H_, W_, C_), dtype=torch.bfloat16, device=self.dev)
-        _chk(lib.rf_unet_mse(self.ctx.handle, _ptr(out32), C_, _ptr(target.contiguous()),
-                             _ptr(mask.contiguous() if mask is not None else None), npix, count, _ptr(dout),
+        # contiguous copies are bound to names: a temporary freed between two
+        # argument evaluations could hand its memory to the next one
+        target = target.contiguous()
+        mask = mask.contiguous() if mask is not None else None
+        _chk(lib.rf_unet_mse(self.ctx.handle, _ptr(out32), C_, _ptr(target), _ptr(mask), npix, count, _ptr(dout),
                              _ptr(loss), s), "mse")
         return loss, dout

@@ -128,6 +128,39 @@ def constant_gb(n, g=(1.0, 0.0, 1.0), b=(0.0, 0.0)):
     return np.ascontiguousarray(np.stack([np.full((n, n), float(v)) for v in vals]).astype(np.float32))
 
 
+def covariate_sample(n, seed, slope_gain=0.5, fuel_gain=0.8, drift_max=0.3):
+    """One synthetic wildfire-like sample on an n x n grid (h = 1/(n-1)),
+    after the paper's synthetic propagation scenarios (App. "Synthetic
+    Propagation Scenarios": terrain g = 1 + alpha |grad z|, high-resistance
+    patches, uniform drift, combined multiplicatively):
+      spatial covariates  z (a 4-mode Fourier terrain, heights up to 0.25)
+                          and fuel (1 inside 3-6 random discs, else 0);
+      global covariates   wind (cos, sin) x speed in [0, 1] and a
+                          temperature in [0, 1];
+      true fields         G = g I with g = (1 + slope_gain |grad z|)
+                          (1 + fuel_gain fuel), b = drift_max speed
+                          (0.5 + 0.5 temperature) (cos, sin), uniform.
+    Returns float32 arrays: Y [n, n, 2] (z, fuel), y [3], gb [5, n, n]."""
+    h = 1.0 / (n - 1)
+    rng = rng_for(seed, 200)
+    z = 0.25 * fourier_field(n, n, h, 4, rng_for(seed, 201))
+    gy, gx = np.gradient(z, h)
+    slope = np.hypot(gx, gy)
+    yy, xx = np.mgrid[0:n, 0:n] * h
+    fuel = np.zeros((n, n))
+    for _ in range(int(rng.integers(3, 7))):
+        cx, cy, r = rng.uniform(0.1, 0.9), rng.uniform(0.1, 0.9), rng.uniform(0.05, 0.15)
+        fuel[(xx - cx) ** 2 + (yy - cy) ** 2 < r * r] = 1.0
+    th, speed, temp = rng.uniform(0, 2 * math.pi), rng.uniform(0, 1), rng.uniform(0, 1)
+    g = (1.0 + slope_gain * slope) * (1.0 + fuel_gain * fuel)
+    bmag = drift_max * speed * (0.5 + 0.5 * temp)
+    gb = np.stack([g, np.zeros_like(g), g, np.full_like(g, bmag * math.cos(th)), np.full_like(g, bmag * math.sin(th))])
+    Y = np.stack([z / 0.25, fuel], axis=-1)
+    y = np.array([speed * math.cos(th), speed * math.sin(th), temp])
+    return dict(Y=Y.astype(np.float32), y=y.astype(np.float32), gb=np.ascontiguousarray(gb.astype(np.float32)),
+                h=h)
+
+
 def constant_fields(ny, nx, M, w, eps=0.0):
     """Constant metric M (2x2 SPD) and drift w, as raw float32 (5, ny, nx)."""
     M = np.asarray(M, dtype=np.float64)
