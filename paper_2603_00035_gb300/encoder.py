@@ -132,7 +132,7 @@ def data_loss(enc, Y, y, sources, obs, targets, h, prm, tv_weight=0.0):
 
 
 def train_synthetic(steps=300, batch=8, n=64, n_sources=2, obs_frac=0.1, lr=2e-3, seed=0, eval_batches=2,
-                    tv_weight=1e-4, log_every=50, device="cuda", alpha=0.5):
+                    tv_weight=0.0, log_every=50, device="cuda", alpha=0.5):
     """Train the encoder on fresh synthetic samples every step; report the
     held-out recovery of G and b and of the arrival times, against the
     untrained encoder and a constant-metric baseline."""
@@ -239,9 +239,10 @@ def main():
     p.add_argument("--obs", type=float, default=0.1)
     p.add_argument("--lr", type=float, default=2e-3)
     p.add_argument("--alpha", type=float, default=0.5)
+    p.add_argument("--tv", type=float, default=0.0)
     a = p.parse_args()
     print(json.dumps(train_synthetic(steps=a.steps, batch=a.batch, n=a.n, n_sources=a.sources, obs_frac=a.obs,
-                                     seed=a.seed, lr=a.lr, alpha=a.alpha)))
+                                     seed=a.seed, lr=a.lr, alpha=a.alpha, tv_weight=a.tv)))
 
 
 if __name__ == "__main__":
