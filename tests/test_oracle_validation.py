@@ -225,3 +225,52 @@ def test_pointwise_gradients_match_finite_differences(name):
             fd = (loss_only(fp, src, h, obs, That) - loss_only(fm, src, h, obs, That)) / (2 * eps)
             den = max(abs(fd), 1e-3 * scale)
             assert abs(grad[c, i, j] - fd) <= 1e-6 * den, (name, (i, j), c, grad[c, i, j], fd)
+
+
+@pytest.mark.parametrize("name", ["isotropic", "anisotropic"])
+def test_gradient_stability_under_metric_noise(name):
+    """1 % metric noise moves the mean gradient by well under 1 % (the paper
+    reports 0.48 %; the reading of the measure is in the fixture)."""
+    g = golden()
+    n = 40
+    fields, src, h, obs, That, grad, _, _ = gradient_case(name, n=n)
+    var = []
+    for k in range(10):
+        r = np.random.default_rng(100 + k)
+        f2 = [f.copy() for f in fields]
+        f2[0] = f2[0] * (1 + 0.01 * r.standard_normal((n, n)))
+        f2[2] = f2[2] * (1 + 0.01 * r.standard_normal((n, n)))
+        _, g2, _ = loss_and_grad(f2, src, h, obs, That)
+        m0, m1 = grad[:3].mean(axis=(1, 2)), g2[:3].mean(axis=(1, 2))
+        var.append(np.abs(m1 - m0).sum() / np.abs(m0).sum())
+    assert 100.0 * np.mean(var) < 2.0 * g["stability_mean_gradient_variation"], np.mean(var)
+
+
+@pytest.mark.parametrize("name", ["isotropic", "anisotropic"])
+def test_random_direction_derivatives(name):
+    """Directional derivatives along 100 random unit directions of the whole
+    parameter space (all five fields at every node): the implicit gradient
+    matches central differences wherever the perturbation keeps every
+    node's active stencil, and with the exactly converged FP64 solve no
+    direction switches a stencil at step 1e-5 here (the paper's 20 %
+    success rate comes from directions that cross stencil boundaries)."""
+    n = 40
+    fields, src, h, obs, That, grad, _, _ = gradient_case(name, n=n)
+    proj, _ = O.project(raw_from_g(*fields), 0.0, 0.05)
+    T0, _, _, _ = O.solve_gs(proj, src, h, 0.0)
+    ids0 = O.record(proj, src, h, 0.0, T0)["id"]
+    eps = 1e-5
+    kept = 0
+    for k in range(100):
+        v = np.random.default_rng(1000 + k).standard_normal((5, n, n))
+        v /= np.linalg.norm(v)
+        fp = [f + eps * v[c] for c, f in enumerate(fields)]
+        fm = [f - eps * v[c] for c, f in enumerate(fields)]
+        pp, _ = O.project(raw_from_g(*fp), 0.0, 0.05)
+        Tp, _, _, _ = O.solve_gs(pp, src, h, 0.0)
+        if (O.record(pp, src, h, 0.0, Tp)["id"] != ids0).any():
+            continue
+        kept += 1
+        fd = (loss_only(fp, src, h, obs, That) - loss_only(fm, src, h, obs, That)) / (2 * eps)
+        assert abs(fd - float((grad * v).sum())) <= 1e-5 * abs(fd), (k, fd)
+    assert kept >= 90
