@@ -217,3 +217,41 @@ class UNet:
         _chk(lib.rf_unet_mse(self.ctx.handle, _ptr(out32), C_, _ptr(target), _ptr(mask), npix, count, _ptr(dout),
                              _ptr(loss), s), "mse")
         return loss, dout
+
+
+def bench_conv(B=8, H=128, W=128, Cin=128, Cout=128, reps=20, tensor_cores=True):
+    """Time one 3x3 convolution layer (BF16 NHWC, FP32 accumulation) with
+    CUDA events: the tcgen05 kernel (tensor_cores=True) or the mma.sync one.
+    Returns (ms per call, TFLOP/s)."""
+    lib, s, ctx = L.load(), _stream(), Context.get(0)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((B, H, W, Cin), generator=g).to(torch.bfloat16).cuda()
+    w = (0.05 * torch.randn((Cout, 3, 3, Cin), generator=g)).to(torch.bfloat16).cuda()
+    bias = torch.zeros(Cout, device="cuda")
+    y = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+    fn = lib.rf_unet_conv3x3_tc if tensor_cores else lib.rf_unet_conv3x3
+    call = lambda: _chk(fn(ctx.handle, _ptr(x), B, H, W, Cin, _ptr(w), _ptr(bias), Cout, 1, _ptr(y), None, s),
+                        "conv3x3")
+    for _ in range(3):
+        call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return ms, 2.0 * B * H * W * Cout * 9 * Cin / (ms * 1e-3) / 1e12
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    p = argparse.ArgumentParser(description="time one 3x3 convolution layer")
+    p.add_argument("--shape", type=int, nargs=5, default=[8, 128, 128, 128, 128], metavar=("B", "H", "W", "CIN", "COUT"))
+    p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--mma-sync", action="store_true", help="time the mma.sync kernel instead of tcgen05")
+    a = p.parse_args()
+    ms, tf = bench_conv(*a.shape, reps=a.reps, tensor_cores=not a.mma_sync)
+    print(json.dumps({"shape": a.shape, "kernel": "mma.sync" if a.mma_sync else "tcgen05", "ms": ms, "tflops": tf}))
