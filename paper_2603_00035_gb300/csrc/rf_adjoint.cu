@@ -245,8 +245,9 @@ __global__ void __launch_bounds__(1024) adjoint_sweep_kernel(AdjArgs a) {
 // warp-sized tickets.  Each lane waits (bounded) until every child named by
 // the record has published its multiplier, gathers them in a fixed
 // neighbour order (no atomics on lambda), and publishes its own multiplier
-// and the epoch of this launch in one 64-bit release store.  The latency
-// chain is the depth of the stencil DAG, not a sweep count.
+// and the epoch of this launch in one 64-bit store (single-copy atomic, no
+// fence: the parent reads nothing else of its child).  The latency chain is
+// the depth of the stencil DAG, not a sweep count.
 
 __global__ void ordered_keys_kernel(const float *T, unsigned *keys, unsigned *vals, long long n) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
