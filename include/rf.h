@@ -293,7 +293,13 @@ rf_status rf_record_stencils(rf_ctx *ctx, const rf_grid *grid,
  * input when opts->mode == RF_MODE_WARM).  stats: HOST pointer, nullable;
  * when given the call synchronises `stream`, fills *stats and returns the
  * device status; when NULL the call is asynchronous and returns after
- * enqueuing. */
+ * enqueuing (launch errors only).  Device-detected errors (not converged,
+ * an expired wait, an empty source mask) live in the shared array's status
+ * word, which the next call clears: they can only be seen by passing stats,
+ * so a caller that must know whether T converged passes it.
+ * The cached device address of the array is valid for the lifetime of the
+ * CUDA context that looked it up: do not use this entry point again after
+ * cudaDeviceReset on that device. */
 rf_status rf_sweep_forward_static(const rf_grid *grid, const float *proj5,
                                   float eps, const uint8_t *src,
                                   const rf_opts *opts, float *T,

@@ -17,7 +17,7 @@
  * Neighbour ring (Fig. 4a): eight neighbours numbered counter-clockwise from
  * the upper-left one; stencil k uses neighbours k and (k+1) mod 8.
  *
- * Readings of the paper used here (each is listed in the design doc):
+ * Readings of the paper used here:
  *  - every finite neighbour contributes its one-point candidate (Eq. 3) and
  *    every stencil with two finite donors contributes its two-point candidate
  *    (Eq. 2) when valid; the node takes the minimum (Sec. 3.2, App. A);
@@ -307,9 +307,10 @@ static int count_sources(int64_t n, const uint8_t *src) {
  * T = 0 on sources, +inf elsewhere.  One iteration = four sweeps in the
  * paper's order: columns left->right, rows along +i, columns right->left,
  * rows along -i; nodes are updated in place, raster order inside a sweep,
- * T <- min(T, min valid candidate).  Stops after the first iteration that
- * changes nothing (exact, since updates only decrease T); the paper's
- * 1e-6 tolerance is replaced by exact no-change in FP64.
+ * T <- min(T, min valid candidate) (replace = 0, the literal Alg. 1) or
+ * T <- min valid candidate (replace = 1; values may then also rise).  Stops
+ * after the first iteration that changes no value bitwise in FP64 (the
+ * paper's 1e-6 tolerance is replaced by exact no-change).
  */
 int orc_solve_gs(int ny, int nx, double h, double eps, const double *L11,
                  const double *L21, const double *L22, const double *wx,

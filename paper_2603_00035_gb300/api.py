@@ -58,6 +58,16 @@ class Context:
     def set_timeout(self, ns: int):
         L.check(L.load().rf_ctx_set_timeout(self.handle, int(ns)), "rf_ctx_set_timeout")
 
+    def raise_on_device_error(self, where: str):
+        """Synchronise the last call's stream and raise RFError when the
+        device status word holds an error (RF_ERR_NOT_CONVERGED,
+        RF_ERR_TIMEOUT, RF_ERR_NONFINITE_INPUT, RF_ERR_NO_SOURCE ...).  The
+        word is cleared by the read, so each error is reported once."""
+        st = self.stats()
+        if st["status"] != L.RF_OK:
+            raise L.RFError(st["status"], where)
+        return st
+
     def stats(self) -> dict:
         st = L.Stats()
         L.load().rf_ctx_last_stats(self.handle, ctypes.byref(st))
@@ -372,8 +382,8 @@ class BatchSolver:
         return g
 
     def grid(self, k, what="T"):
-        """Result of the caller's grid k: T (ny, nx), graw (5, ny, nx) or the
-        record fields."""
+        """Result of the caller's grid k: T (ny, nx), graw (5, ny, nx), the
+        record fields (id, w1) or the per-grid status."""
         slot = self.order.index(k)
         o = self.offsets[slot]
         ny, nx = self.shapes[slot]
@@ -383,6 +393,8 @@ class BatchSolver:
             return self.graw[:, o:o + ny * nx].reshape(5, ny, nx)
         if what == "id":
             return self.rec.id[o:o + ny * nx].view(ny, nx)
+        if what == "w1":
+            return self.rec.w1[o:o + ny * nx].view(ny, nx)
         if what == "status":
             return self.gstat[slot]
         raise ValueError(what)

@@ -8,6 +8,12 @@ Eqs. 4-6; Alg. 2): the saved state is T, the stencil record (ids, donor
 weights, closed-form partials), the raw fields and the clip mask -- not the
 sweep history -- so memory is O(nodes) whatever the sweep count.  Every
 step runs in librf's CUDA kernels; this module only wires them to autograd.
+
+Device-detected errors are not silent: after the forward solve and after the
+adjoint the context's status word is read (which synchronises the stream),
+and a non-converged solve, an expired device wait, a non-finite input or an
+empty source mask raises RFError instead of returning gradients of an
+unusable T.
 """
 from __future__ import annotations
 
@@ -30,6 +36,7 @@ class RFSolve(torch.autograd.Function):
         raw5 = raw5.contiguous()
         proj, clip = api.rf_project(raw5, eps, delta)
         T, rec = api.rf_sweep_forward(proj, eps, src, h, opts=opts)
+        api.Context.get(raw5.device).raise_on_device_error("RFSolve.forward")
         ctx.save_for_backward(raw5, clip, src, T, rec.id, rec.w1, rec.dT)
         ctx.cfg = (eps, delta, algo)
         return T
@@ -42,6 +49,7 @@ class RFSolve(torch.autograd.Function):
         rec = api.Record(rid, rw1, rdT)
         gproj, _ = api.rf_adjoint(src, T, rec, g, algo=algo, lam=False)
         graw = api.rf_project_backward(raw5, clip, eps, delta, gproj)
+        api.Context.get(raw5.device).raise_on_device_error("RFSolve.backward")
         return graw, None, None, None, None, None, None
 
 
@@ -82,6 +90,7 @@ class SweepSolve(torch.autograd.Function):
     def forward(ctx, proj5, src, h, eps=1e-6, algo="ordered", opts=None):
         proj5 = proj5.contiguous()
         T, rec = api.rf_sweep_forward(proj5, eps, src, h, opts=opts)
+        api.Context.get(proj5.device).raise_on_device_error("SweepSolve.forward")
         ctx.save_for_backward(src, T, rec.id, rec.w1, rec.dT)
         ctx.algo = algo
         return T
@@ -91,6 +100,7 @@ class SweepSolve(torch.autograd.Function):
         src, T, rid, rw1, rdT = ctx.saved_tensors
         g = torch.nan_to_num(gT.contiguous().to(torch.float32), nan=0.0, posinf=0.0, neginf=0.0)
         gproj, _ = api.rf_adjoint(src, T, api.Record(rid, rw1, rdT), g, algo=ctx.algo, lam=False)
+        api.Context.get(T.device).raise_on_device_error("SweepSolve.backward")
         return gproj, None, None, None, None, None
 
 

@@ -797,7 +797,9 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
   if (cudaLaunchCooperativeKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, s) !=
       cudaSuccess)
     return RF_ERR_CUDA;
-  if (!stats) return RF_OK;
+  // asynchronous path: report launch errors of the init kernels here rather
+  // than leaving them to whatever call comes next
+  if (!stats) return cuda_status(cudaGetLastError());
   DevState h;
   if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

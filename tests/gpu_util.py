@@ -6,8 +6,15 @@ Tolerances (the parity bar):
 * forward: max |T_gpu - T_oracle| <= 1e-4 * max T over reached nodes, and
   the reached set identical;
 * gradients: relative L2 <= 1e-3 over nodes outside the flip set;
-* flip set: nodes whose stencil id differs between GPU and oracle, or whose
-  oracle best-vs-second valid candidate margin is < 1e-5 * max T.
+* stencils are compared in canonical form: a two-point update whose donor
+  weight is within DEGENERATE of 1 (or 0) is the one-point update through its
+  first (second) donor -- same value, same partials to that order -- so the
+  two namings of one update are not a mismatch;
+* near-tie: the oracle's best-vs-second valid candidate margin is
+  < 1e-5 * max T (FP32 may legitimately pick either candidate there);
+* flip set: nodes whose canonical stencils differ; every flip must be a
+  near-tie (a mismatch outside the near-ties fails), flips are excluded from
+  the gradient comparison and their fraction is bounded per workload.
 """
 import numpy as np
 import pytest
@@ -21,6 +28,7 @@ from paper_2603_00035_gb300 import build as B  # noqa: E402
 FWD_TOL = 1e-4
 GRAD_TOL = 1e-3
 FLIP_MARGIN = 1e-5
+DEGENERATE = 1e-4
 
 
 def require_gpu():
@@ -58,10 +66,34 @@ def oracle_path(raw, src, h, eps, delta, g):
     return O.solve_and_grad(np.asarray(raw, np.float64), src, h, eps, delta, np.asarray(g, np.float64))
 
 
+def canonical_stencil(ids, w1):
+    """Record ids with degenerate two-point updates renamed to the one-point
+    update they equal: 0x20|k with w1 >= 1 - DEGENERATE -> 0x10|k, with
+    w1 <= DEGENERATE -> 0x10|((k + 1) % 8)."""
+    ids = np.asarray(ids).astype(np.int32)
+    w1 = np.asarray(w1)
+    two = (ids & 0xF0) == 0x20
+    k = ids & 7
+    out = ids.copy()
+    out = np.where(two & (w1 >= 1.0 - DEGENERATE), 0x10 | k, out)
+    out = np.where(two & (w1 <= DEGENERATE), 0x10 | ((k + 1) & 7), out)
+    return out
+
+
+def stencil_compare(gpu_id, gpu_w1, orc_rec, tmax):
+    """(flips, hard): flips = canonical stencils differ; hard = flips that
+    are not near-ties of the oracle (must be empty)."""
+    a = canonical_stencil(gpu_id, gpu_w1)
+    b = canonical_stencil(orc_rec["id"], orc_rec["w1"])
+    flips = a != b
+    hard = flips & (orc_rec["margin"] >= FLIP_MARGIN * tmax)
+    return flips, hard
+
+
 def flip_mask(gpu, orc):
     T = orc["T"]
     tmax = T[np.isfinite(T)].max()
-    flips = (gpu["rec_np"]["id"] != orc["rec"]["id"]) | (orc["rec"]["margin"] < FLIP_MARGIN * tmax)
+    flips, _ = stencil_compare(gpu["rec_np"]["id"], gpu["rec_np"]["w1"], orc["rec"], tmax)
     return flips, tmax
 
 

@@ -68,8 +68,8 @@ def test_rfsolve_gradients_match_oracle(which, algo):
     To, _, _, _ = O.solve_gs(proj, src, h, eps)
     g_o = obs * (To - That)
     orc = O.solve_and_grad(raw.astype(np.float64), src, h, eps, delta, g_o)
-    gpu_like = dict(rec_np=dict(id=api.rf_sweep_forward(api.rf_project(to_dev(raw, torch.float32), eps, delta)[0],
-                                                         eps, src_t, h)[1].id.cpu().numpy()))
+    rec_g = api.rf_sweep_forward(api.rf_project(to_dev(raw, torch.float32), eps, delta)[0], eps, src_t, h)[1]
+    gpu_like = dict(rec_np=dict(id=rec_g.id.cpu().numpy(), w1=rec_g.w1.cpu().numpy()))
     flips, _ = flip_mask(gpu_like, orc)
     err = rel_l2(g_gpu, orc["graw"], ~flips)
     assert err < GRAD_TOL, (which, algo, err, int(flips.sum()))

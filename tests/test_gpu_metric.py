@@ -183,8 +183,9 @@ def test_paper_parameterisation_gradients_match_oracle():
     _, tvb = MR.tv_drift(*gbp_o[3:])
     dgbp = np.stack([1e-3 * g for g in tvg] + [1e-3 * g for g in tvb])
     want = MR.metric_project_backward(gb, LMIN, LMAX, BMAX, DELTA, EPS, dproj5=gproj, dgbp5=dgbp)
-    ids = api.rf_sweep_forward(api.rf_metric_project(to_dev(gb), p, want_gbp=False)[1], EPS, src_t, h)[1].id
-    flips, _ = flip_mask(dict(rec_np=dict(id=ids.cpu().numpy())), dict(T=To, rec=rec))
+    rec_g = api.rf_sweep_forward(api.rf_metric_project(to_dev(gb), p, want_gbp=False)[1], EPS, src_t, h)[1]
+    flips, _ = flip_mask(dict(rec_np=dict(id=rec_g.id.cpu().numpy(), w1=rec_g.w1.cpu().numpy())),
+                         dict(T=To, rec=rec))
     mask = ~flips & away_from_kinks(gb)
     assert rel_l2(g_gpu, want, mask) < 1e-3, rel_l2(g_gpu, want, mask)
 

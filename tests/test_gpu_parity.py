@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 import rf_inputs as R
-from gpu_util import (FWD_TOL, GRAD_TOL, api, flip_mask, gpu_path, oracle_path, rel_l2, require_gpu, to_dev,
-                      torch)
+from gpu_util import (FWD_TOL, GRAD_TOL, api, flip_mask, gpu_path, oracle_path, rel_l2, require_gpu,
+                      stencil_compare, to_dev, torch)
 import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -58,14 +58,23 @@ def test_forward_parity(case):
     assert np.all(Tg[c["src"] == 1] == 0.0)
 
 
+# bound on the fraction of nodes whose (canonical) stencil differs from the
+# oracle's -- all of them near-ties -- per workload
+FLIP_BOUND = {"config1": 0.01, "ragged": 0.01, "config2": 0.01}
+
+
 def test_record_parity(case):
     name, c, gpu, orc = case
-    flips, tmax = flip_mask(gpu, orc)
+    T = orc["T"]
+    tmax = T[np.isfinite(T)].max()
+    flips, hard = stencil_compare(gpu["rec_np"]["id"], gpu["rec_np"]["w1"], orc["rec"], tmax)
+    raw_diff = gpu["rec_np"]["id"] != orc["rec"]["id"]
+    print(f"{name}: ids differ {raw_diff.mean():.4f}, canonical flips {flips.mean():.5f} "
+          f"({int(flips.sum())} nodes), hard mismatches {int(hard.sum())}")
     # near-ties (oracle margin < 1e-5 max T) may pick either stencil; outside
     # them the GPU must name the oracle's stencil
-    hard = (gpu["rec_np"]["id"] != orc["rec"]["id"]) & (orc["rec"]["margin"] >= 1e-5 * tmax)
-    assert hard.mean() < 1e-3, (name, hard.sum(), flips.mean())
-    print(f"{name}: near-tie/flip fraction {flips.mean():.4f}, hard mismatches {int(hard.sum())}")
+    assert int(hard.sum()) == 0, (name, np.argwhere(hard)[:10])
+    assert flips.mean() <= FLIP_BOUND[name], (name, flips.mean())
     keep = ~flips
     assert np.allclose(gpu["rec_np"]["w1"][keep], orc["rec"]["w1"][keep], atol=2e-3)
     dTg, dTo = gpu["rec_np"]["dT"], orc["rec"]["dT"]

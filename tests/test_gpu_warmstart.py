@@ -4,6 +4,7 @@ against the cold solve and the residual check."""
 import numpy as np
 import pytest
 
+import oracle as O
 import rf_inputs as R
 from gpu_util import FWD_TOL, require_gpu, to_dev, torch
 from paper_2603_00035_gb300 import api, warmstart as WS
@@ -66,3 +67,27 @@ def test_trained_network_warm_start_is_correct_and_measured():
     assert (Tw - Tc).abs().max().item() <= FWD_TOL * Tc.max().item()
     assert info["residual"] <= 1e-5 * Tc.max().item() or info["fallback"]
     print(f"cold sweeps {stc['sweeps']}, warm sweeps {info['warm_sweeps']}, fallback {info['fallback']}")
+
+
+def test_warm_solve_without_fallback_matches_oracle():
+    """A warm-started 1024^2 solve from the network's resampled guess, run to
+    its own fixed point (sweep cap high enough that the cold fallback never
+    fires), against the FP64 oracle: identical reached set and max |dT| <=
+    1e-4 max T."""
+    net, _ = WS.train(samples=64, chunk=64, batch=8)
+    n = 1024
+    h = 1.0 / (n - 1)
+    raw_np = R.randers_fields(n, n, h, 16, 78, omega="unit", omega_scale=0.3)
+    src_np = R.random_sources(n, n, 2, 78)
+    Tw, info = WS.solve(net, torch.from_numpy(raw_np).cuda(), torch.from_numpy(src_np).cuda(), h,
+                        opts=api.make_opts(max_sweeps=1000))
+    assert not info["fallback"], info
+    prj, _ = O.project(raw_np.astype(np.float64), 1e-6, 0.05)
+    To, _, st, _ = O.solve_gs(prj, src_np, h, 1e-6)
+    assert st == O.OK
+    Tw = Tw.cpu().numpy()
+    assert np.array_equal(np.isfinite(Tw), np.isfinite(To))
+    fin = np.isfinite(To)
+    err = np.abs(Tw[fin] - To[fin]).max()
+    print(f"warm 1024^2: sweeps {info['warm_sweeps']}, max |dT| / max T = {err / To[fin].max():.2e}")
+    assert err <= FWD_TOL * To[fin].max()

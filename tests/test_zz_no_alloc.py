@@ -50,10 +50,14 @@ def test_static_entry_matches_allocating_entry_twice():
     for call in range(2):
         T = torch.full((ny, nx), float("nan"), dtype=torch.float32, device="cuda")
         st = L.Stats()
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         status = fn(ctypes.byref(grid), ctypes.c_void_p(proj.data_ptr()), c["eps"],
                     ctypes.c_void_p(src.data_ptr()), ctypes.byref(opts), ctypes.c_void_p(T.data_ptr()),
                     ctypes.byref(st), stream)
         assert status == L.RF_OK, (call, L.STATUS.get(status, status))
+        if call == 1:  # the first call may load the module; the second must not allocate anything
+            assert torch.cuda.mem_get_info()[0] == free_before, "the call allocated device memory"
         assert st.converged == 1 and st.sweeps == st_ref["sweeps"], (call, st.sweeps, st_ref["sweeps"])
         err = (T - T_ref).abs().max().item()
         assert err <= FWD_TOL * tmax, (call, err)
@@ -73,3 +77,25 @@ def test_static_entry_rejects_oversized_grids():
     opts = api.make_opts(max_sweeps=5000)  # beyond the 1024-sweep limit
     assert fn(ctypes.byref(grid), p, 1e-6, p, ctypes.byref(opts), p, ctypes.byref(st), None) == \
         L.RF_ERR_INVALID_ARG
+
+
+def test_static_entry_warm_mode_asynchronous():
+    """Warm mode with stats = NULL (the asynchronous path): start from 1.2 x
+    the allocating entry's solution, synchronise, and compare."""
+    require_gpu()
+    fn = _static_fn()
+    c = R.config1()
+    ny, nx = c["src"].shape
+    proj, _ = api.rf_project(to_dev(c["raw"], torch.float32), c["eps"], c["delta"])
+    src = to_dev(c["src"], torch.uint8)
+    T_ref, _ = api.rf_sweep_forward(proj, c["eps"], src, c["h"], opts=api.make_opts(variant="tiled1"), record=False)
+    assert api.Context.get(0).stats()["status"] == 0
+    T = (T_ref * 1.2).contiguous()
+    grid = L.Grid(ny, nx, c["h"])
+    opts = api.make_opts(warm=True, max_sweeps=256)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    status = fn(ctypes.byref(grid), ctypes.c_void_p(proj.data_ptr()), c["eps"], ctypes.c_void_p(src.data_ptr()),
+                ctypes.byref(opts), ctypes.c_void_p(T.data_ptr()), None, stream)
+    assert status == L.RF_OK, L.STATUS.get(status, status)
+    torch.cuda.synchronize()
+    assert (T - T_ref).abs().max().item() <= FWD_TOL * T_ref.max().item()
