@@ -64,8 +64,10 @@ enum rf_adjoint_algo {
   RF_ADJ_ORDERED = 1 /* radix sort on T, then dependency-ordered gather     */
 };
 
-/* Forward-sweep kernel variants (all run the same schedule and update;
- * they differ in how a line step gets its per-node constants).
+/* Forward-solve kernel variants.  The first three run the paper's schedule
+ * (Sec. 3.2: column/row line fronts, sweeps in alternating directions) and
+ * differ in how a line step gets its per-node constants; TILES runs another
+ * schedule to the same fixed point.
  *  TILED1    node tables built per block in shared memory, one thread per
  *            node evaluates all 16 candidates;
  *  STREAMED  node records (24 floats) computed once per solve into a
@@ -73,14 +75,25 @@ enum rf_adjoint_algo {
  *            copied per line step by the bulk-copy engine; one thread per
  *            node, two-point candidates in the cone form (same values up to
  *            FP32 rounding);
- *  TILED4    as TILED1 with four threads per node and a shuffle minimum.
- * AUTO = STREAMED when its shape fits the device and the record buffer can
- * be allocated, else TILED1. */
+ *  TILED4    as TILED1 with four threads per node and a shuffle minimum;
+ *  TILES     tile queue: 32 x 32 tiles iterated (Jacobi, one thread per
+ *            node, constants in registers) to a local fixed point with
+ *            their halo ring fixed; a tile whose boundary moved queues its
+ *            neighbours for the next round, and each round processes the
+ *            queued tiles within a window of the smallest arrival time
+ *            (delta-stepping); deterministic (tiles read their neighbours'
+ *            state as of the round's start).  Same fixed point as the line
+ *            sweeps (every node at T = min valid candidate(T) to the change
+ *            tolerance), a dependent chain of iterations along the front
+ *            instead of sweeps x grid lines.
+ * AUTO = TILES when its workspace can be allocated, else STREAMED when its
+ * shape fits the device, else TILED1. */
 enum rf_sweep_variant {
   RF_SWEEP_AUTO = 0,
   RF_SWEEP_TILED1 = 1,
   RF_SWEEP_STREAMED = 2,
-  RF_SWEEP_TILED4 = 4
+  RF_SWEEP_TILED4 = 4,
+  RF_SWEEP_TILES = 8
 };
 
 typedef struct rf_opts {
@@ -97,6 +110,10 @@ typedef struct rf_opts {
                          can turn into an ulp-level 2-cycle; the default
                          (opts NULL) is tol 0, rtol 1e-6 (about 8 ulp)     */
   int32_t variant;    /* enum rf_sweep_variant (0 = auto)                   */
+  float window;       /* TILES: a round processes the queued tiles whose
+                         key (smallest new boundary time that queued them)
+                         is within window x 32 x (mean edge cost) of the
+                         smallest key (0 = auto: 2)                        */
 } rf_opts;
 
 /* Per-node record of the converged forward solve (Alg. 2, first loop). */
@@ -110,12 +127,14 @@ typedef struct rf_record {
 
 typedef struct rf_stats {
   int32_t status;       /* rf_status found on the device                  */
-  int32_t sweeps;       /* directional sweeps run (forward) / adjoint     */
+  int32_t sweeps;       /* directional sweeps run (forward; TILES: node
+                           updates / nodes, rounded up)                   */
   int32_t converged;    /* 1 if the last sweep changed nothing            */
   int32_t adj_sweeps;   /* sweeps of the last adjoint (RF_ADJ_SWEEP)      */
-  int64_t cell_updates; /* sweeps * ny * nx of the last forward           */
+  int64_t cell_updates; /* node updates of the last forward (line sweeps:
+                           sweeps * ny * nx; TILES: nodes evaluated)      */
   float max_residual;   /* max |T - min valid candidate(T)| (record pass) */
-  float pad;
+  int32_t rounds;       /* rounds of the last TILES solve (0 otherwise)     */
 } rf_stats;
 
 /* ---- context ------------------------------------------------------------
@@ -257,7 +276,8 @@ rf_status rf_encoder_combine_backward(rf_ctx *ctx, const float *dgb, int B,
  * dT0/dtheta of every node's winning update at the converged T are written
  * (Alg. 2 "Identify active stencil"; App. A closed-form partials), plus the
  * max residual into the stats.  opts may be NULL (defaults: tol 0, rtol 1e-6,
- * max_sweeps 64, cold start, automatic band/block). */
+ * max_sweeps 64, cold start, automatic variant and shape).  TILES caps its
+ * rounds at max_sweeps x (tiles along the longer side). */
 rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid,
                            const float *proj5, float eps, const uint8_t *src,
                            const rf_opts *opts, float *T, rf_record *rec,

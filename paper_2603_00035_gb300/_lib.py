@@ -17,7 +17,7 @@ STATUS = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_CUDA", 3: "RF_ERR_NOT_
           7: "RF_ERR_NO_MEMORY", 8: "RF_ERR_UNSUPPORTED"}
 RF_OK, RF_ERR_INVALID_ARG, RF_ERR_CUDA, RF_ERR_NOT_CONVERGED, RF_ERR_TIMEOUT = 0, 1, 2, 3, 4
 RF_ERR_NONFINITE_INPUT, RF_ERR_NO_SOURCE, RF_ERR_NO_MEMORY, RF_ERR_UNSUPPORTED = 5, 6, 7, 8
-RF_SWEEP_AUTO, RF_SWEEP_TILED1, RF_SWEEP_STREAMED, RF_SWEEP_TILED4 = 0, 1, 2, 4
+RF_SWEEP_AUTO, RF_SWEEP_TILED1, RF_SWEEP_STREAMED, RF_SWEEP_TILED4, RF_SWEEP_TILES = 0, 1, 2, 4, 8
 RF_MODE_COLD, RF_MODE_WARM = 0, 1
 RF_ADJ_SWEEP, RF_ADJ_ORDERED = 0, 1
 
@@ -35,7 +35,7 @@ class Grid(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("max_sweeps", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("band", ctypes.c_int32), ("block", ctypes.c_int32), ("rtol", ctypes.c_float),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("window", ctypes.c_float)]
 
 
 class MetricParams(ctypes.Structure):
@@ -58,7 +58,7 @@ class BatchDesc(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("adj_sweeps", ctypes.c_int32), ("cell_updates", ctypes.c_int64),
-                ("max_residual", ctypes.c_float), ("pad", ctypes.c_float)]
+                ("max_residual", ctypes.c_float), ("rounds", ctypes.c_int32)]
 
 
 _lib = None

@@ -73,7 +73,7 @@ class Context:
         L.load().rf_ctx_last_stats(self.handle, ctypes.byref(st))
         return dict(status=st.status, status_name=L.STATUS.get(st.status, str(st.status)), sweeps=st.sweeps,
                     converged=bool(st.converged), adj_sweeps=st.adj_sweeps, cell_updates=st.cell_updates,
-                    max_residual=st.max_residual)
+                    max_residual=st.max_residual, rounds=st.rounds)
 
     def __del__(self):
         try:
@@ -197,17 +197,19 @@ def rf_tv(gb5, metric="frobenius", w_metric=1.0, w_drift=1.0, grad5=None, value=
 
 
 SWEEP_VARIANTS = {"auto": L.RF_SWEEP_AUTO, "tiled1": L.RF_SWEEP_TILED1, "streamed": L.RF_SWEEP_STREAMED,
-                  "tiled4": L.RF_SWEEP_TILED4}
+                  "tiled4": L.RF_SWEEP_TILED4, "tiles": L.RF_SWEEP_TILES}
 
 
-def make_opts(tol=0.0, max_sweeps=64, warm=False, band=0, block=0, rtol=1e-6, variant=0):
+def make_opts(tol=0.0, max_sweeps=64, warm=False, band=0, block=0, rtol=1e-6, variant=0, window=0.0):
     """rf_opts: a node counts as changed when |dT| > tol + rtol * T (tol =
-    rtol = 0: bitwise); the sweep stops at the first sweep with no change.
-    band/block: line-tile shape (0 = auto); variant: forward-sweep kernel,
-    a name of SWEEP_VARIANTS or its value (0 = auto)."""
+    rtol = 0: bitwise); the solve stops at a state where no node changes.
+    band/block: line-tile shape of the line-sweep variants (0 = auto);
+    variant: forward kernel, a name of SWEEP_VARIANTS or its value (0 =
+    auto); window: the tile queue's delta-stepping window in tile crossings
+    (0 = auto)."""
     v = SWEEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
     return L.Opts(float(tol), int(max_sweeps), L.RF_MODE_WARM if warm else L.RF_MODE_COLD, int(band), int(block),
-                  float(rtol), v)
+                  float(rtol), v, float(window))
 
 
 def rf_sweep_forward(proj5, eps, src, h, opts=None, T=None, record=True, rec=None, ctx=None, stream=None):

@@ -39,6 +39,7 @@ extern "C" rf_status rf_ctx_destroy(rf_ctx *c) {
   cudaFree(c->adj_state);
   cudaFree(c->recbuf);
   cudaFree(c->tvbuf);
+  cudaFree(c->tilebuf);
   delete c;
   return RF_OK;
 }
@@ -65,6 +66,7 @@ extern "C" rf_status rf_ctx_last_stats(rf_ctx *c, rf_stats *out) {
   float mr;
   std::memcpy(&mr, &s.max_res_bits, sizeof(mr));
   out->max_residual = mr;
+  out->rounds = (int32_t)s.rounds;
   // the status word reports errors since the previous call: clear it
   int zero = 0;
   if (cudaMemcpy(&c->state->status, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -34,6 +34,8 @@ struct rf_ctx {
   size_t recbuf_cap = 0;
   float *tvbuf = nullptr;  // total variation: per-block partial sums
   size_t tvbuf_cap = 0;
+  unsigned char *tilebuf = nullptr;  // tile-queue solve: queue, tile states, halos
+  size_t tilebuf_cap = 0;
 };
 
 namespace rf {

@@ -247,7 +247,7 @@ struct DevState {
   unsigned bar_count;  // grid barrier arrivals
   unsigned bar_gen;    // grid barrier generation
   unsigned max_res_bits;  // float bits of max |residual| (non-negative)
-  unsigned pad;
+  unsigned rounds;        // rounds of the last tile-queue solve
   unsigned long long cell_updates;
 };
 

@@ -30,6 +30,7 @@
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
 #include "rf_sweep_stream.h"
+#include "rf_sweep_tiles.h"
 
 namespace rf {
 
@@ -511,7 +512,8 @@ rf_status plan_sweep(rf_ctx *ctx, int ny, int nx, const rf_opts *o, int lanes, S
 }
 
 bool variant_ok(int v) {
-  return v == RF_SWEEP_AUTO || v == RF_SWEEP_TILED1 || v == RF_SWEEP_STREAMED || v == RF_SWEEP_TILED4;
+  return v == RF_SWEEP_AUTO || v == RF_SWEEP_TILED1 || v == RF_SWEEP_STREAMED || v == RF_SWEEP_TILED4 ||
+         v == RF_SWEEP_TILES;
 }
 
 }  // namespace
@@ -522,9 +524,10 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   if (!ctx || !grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
   if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
   if (rec && (!rec->id || !rec->w1 || !rec->dT)) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0, 0.0f};
   if (opts) o = *opts;
-  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM) ||
+      !(o.window >= 0.0f))
     return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -533,6 +536,51 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   const long long n = (long long)ny * nx;
 
   if (!variant_ok(o.variant)) return RF_ERR_INVALID_ARG;
+
+  // tile queue: the default when its workspace can be allocated
+  if (o.variant == RF_SWEEP_TILES || o.variant == RF_SWEEP_AUTO) {
+    rf_status rt = ensure(&ctx->tilebuf, &ctx->tilebuf_cap, rf::tile_work_bytes(ny, nx));
+    if (rt == RF_OK) rt = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)n);
+    if (rt == RF_OK) rt = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2);
+    if (rt != RF_OK && o.variant == RF_SWEEP_TILES) return rt;
+    if (rt == RF_OK) {
+      cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
+      cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
+      cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 4, s);
+      cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
+      int *has_src = ctx->changed + o.max_sweeps;
+      init_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, src, n, o.mode == RF_MODE_WARM,
+                                                                         ctx->state, has_src);
+      check_source_kernel<<<1, 32, 0, s>>>(has_src, ctx->state);
+      LaunchCtl ctl;
+      ctl.st = ctx->state;
+      ctl.abort = ctx->changed + o.max_sweeps + 1;
+      ctl.timeout_ns = ctx->timeout_ns;
+      const rf::TileWork w = rf::tile_work_carve(ctx->tilebuf, ny, nx);
+      rt = rf::tiles_launch(ctx->device, ctx->num_sms, ny, nx, grid->h, eps, proj5, src, T, ctx->tbuf,
+                            o.mode == RF_MODE_WARM, o.max_sweeps, o.tol, o.rtol, o.window, w, ctl, s);
+      if (rt != RF_OK) return rt;
+      if (rec) {
+        RecordArgs r;
+        r.ny = ny;
+        r.nx = nx;
+        r.h = grid->h;
+        r.eps = eps;
+        r.f = proj5;
+        r.src = src;
+        r.T = T;
+        r.id = rec->id;
+        r.w1 = rec->w1;
+        r.dT = rec->dT;
+        r.res = nullptr;
+        r.max_abs = nullptr;
+        r.st = ctx->state;
+        cudaMemsetAsync(&ctx->state->max_res_bits, 0, sizeof(unsigned), s);
+        record_kernel<true><<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(r);
+      }
+      return cuda_status(cudaGetLastError());
+    }
+  }
 
   // kernel variant: streamed when requested or automatic and it fits,
   // else tiled (one or four threads per node)
@@ -561,7 +609,7 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   cudaMemsetAsync(ctx->progress, 0, sizeof(unsigned) * (grid_ctas + 1), s);
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
   cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
-  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 3, s);
+  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 4, s);
   cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
 
   int *has_src = ctx->changed + o.max_sweeps;  // last slot
@@ -720,7 +768,7 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
                                              rf_stats *stats, void *stream) {
   if (!grid_ok(grid) || !proj5 || !src || !T) return RF_ERR_INVALID_ARG;
   if (!(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0, 0.0f};
   if (opts) o = *opts;
   if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
     return RF_ERR_INVALID_ARG;
@@ -749,9 +797,10 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
   planner.device = dev;
   if (cudaDeviceGetAttribute(&planner.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return RF_ERR_CUDA;
-  // the streamed variant needs a record buffer: not available without
-  // allocation
-  if (o.variant == RF_SWEEP_STREAMED || !variant_ok(o.variant)) return RF_ERR_INVALID_ARG;
+  // the streamed variant needs a record buffer and the tile queue its queue
+  // workspace: neither is available without allocation
+  if (o.variant == RF_SWEEP_STREAMED || o.variant == RF_SWEEP_TILES || !variant_ok(o.variant))
+    return RF_ERR_INVALID_ARG;
   SweepPlan pl;
   rf_status rs = plan_sweep(&planner, ny, nx, &o, o.variant == RF_SWEEP_TILED4 ? 4 : 1, &pl);
   if (rs != RF_OK) return rs;
@@ -810,6 +859,6 @@ extern "C" rf_status rf_sweep_forward_static(const rf_grid *grid, const float *p
   stats->adj_sweeps = 0;
   stats->cell_updates = (int64_t)h.cell_updates;
   stats->max_residual = 0.0f;
-  stats->pad = 0.0f;
+  stats->rounds = 0;
   return (rf_status)h.status;
 }

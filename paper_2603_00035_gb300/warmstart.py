@@ -170,7 +170,7 @@ def solve(net, raw5, src, h, eps=1e-6, delta=0.05, opts=None, residual_tol=None,
         T.mul_(inflate)
     o = opts if opts is not None else api.make_opts()
     ow = api.make_opts(tol=o.tol, max_sweeps=o.max_sweeps, warm=True, band=o.band, block=o.block, rtol=o.rtol,
-                       variant=o.variant)
+                       variant=o.variant, window=o.window)
     api.rf_sweep_forward(proj, eps, src, h, opts=ow, T=T, record=False)
     st = ctx.stats()
     res = float(api.rf_residual(proj, eps, src, h, T).item())

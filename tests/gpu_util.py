@@ -66,18 +66,32 @@ def oracle_path(raw, src, h, eps, delta, g):
     return O.solve_and_grad(np.asarray(raw, np.float64), src, h, eps, delta, np.asarray(g, np.float64))
 
 
-def canonical_stencil(ids, w1):
+def canonical_stencil(ids, w1, with_weight=False):
     """Record ids with degenerate two-point updates renamed to the one-point
     update they equal: 0x20|k with w1 >= 1 - DEGENERATE -> 0x10|k, with
-    w1 <= DEGENERATE -> 0x10|((k + 1) % 8)."""
+    w1 <= DEGENERATE -> 0x10|((k + 1) % 8).  with_weight: also the donor
+    weight in the same form (1 for a renamed update, as for a one-point)."""
     ids = np.asarray(ids).astype(np.int32)
     w1 = np.asarray(w1)
     two = (ids & 0xF0) == 0x20
     k = ids & 7
-    out = ids.copy()
-    out = np.where(two & (w1 >= 1.0 - DEGENERATE), 0x10 | k, out)
-    out = np.where(two & (w1 <= DEGENERATE), 0x10 | ((k + 1) & 7), out)
+    hi, lo = two & (w1 >= 1.0 - DEGENERATE), two & (w1 <= DEGENERATE)
+    out = np.where(hi, 0x10 | k, ids)
+    out = np.where(lo, 0x10 | ((k + 1) & 7), out)
+    if with_weight:
+        return out, np.where(hi | lo, 1.0, w1)
     return out
+
+
+def describe_mismatch(mask, gpu_id, gpu_w1, gpu_T, orc_rec, orc_T, limit=6):
+    """Text dump of the first nodes of `mask` (for assertion messages)."""
+    tmax = orc_T[np.isfinite(orc_T)].max()
+    rows = []
+    for i, j in np.argwhere(mask)[:limit]:
+        rows.append(f"({i},{j}) gpu id {int(gpu_id[i, j]):#x} w1 {float(gpu_w1[i, j]):.5f} T {float(gpu_T[i, j]):.7g}"
+                    f" | oracle id {int(orc_rec['id'][i, j]):#x} w1 {float(orc_rec['w1'][i, j]):.5f}"
+                    f" T {float(orc_T[i, j]):.7g} margin/maxT {float(orc_rec['margin'][i, j]) / tmax:.2e}")
+    return "\n".join(rows)
 
 
 def stencil_compare(gpu_id, gpu_w1, orc_rec, tmax):

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import rf_inputs as R
-from gpu_util import FWD_TOL, GRAD_TOL, rel_l2, require_gpu, stencil_compare, to_dev, torch
+from gpu_util import FWD_TOL, GRAD_TOL, describe_mismatch, rel_l2, require_gpu, stencil_compare, to_dev, torch
 from paper_2603_00035_gb300 import api
 
 pytestmark = pytest.mark.gpu
@@ -155,6 +155,6 @@ def test_batch_config3_sizes_match_oracle():
         w1 = bs.grid(k, "w1").cpu().numpy()
         flips, hard = stencil_compare(ids, w1, orc["rec"], tmax)
         print(f"grid {k} {g['src'].shape} sources {g['nsrc']}: flips {flips.mean():.5f}, hard {int(hard.sum())}")
-        assert int(hard.sum()) == 0, (k, g["src"].shape)
+        assert int(hard.sum()) == 0, (k, g["src"].shape, describe_mismatch(hard, ids, w1, Tb, orc["rec"], To))
         assert flips.mean() <= 0.01, (k, flips.mean())
         assert rel_l2(bs.grid(k, "graw").cpu().numpy(), orc["graw"], ~flips) < GRAD_TOL, (k, g["src"].shape)
