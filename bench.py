@@ -35,11 +35,13 @@ sys.path.insert(0, ROOT)
 METRIC = "forward+adjoint solves/s at 2048x2048"
 UNIT = "solves/s"
 ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-update
-# kernels of ours per step: project, init, source check, sweep, record, project backward, plus the
-# adjoint's own kernels (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not counted);
-# the streamed forward variant adds its node-record kernel
-LAUNCHES_PER_STEP = {"sweep": 7, "ordered": 9}
-STREAMED = 2
+# kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
+# source check, then tile queue: seed, queue, finish-seed, solve, stats; streamed: node records + sweep;
+# tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not
+# counted)
+LAUNCHES_BASE = 3
+LAUNCHES_FORWARD = {8: 7, 2: 4, 1: 3, 4: 3}
+LAUNCHES_ADJOINT = {"sweep": 1, "ordered": 3}
 
 
 def parse():
@@ -52,7 +54,9 @@ def parse():
     p.add_argument("--algo", default="ordered", choices=["sweep", "ordered"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--block", type=int, default=0)
-    p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 4])
+    p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                   help="forward kernel (0: autotuned; 8 tile queue, 2 streamed, 1/4 tiled line sweeps)")
+    p.add_argument("--window", type=float, default=0.0, help="tile queue window (0: kernel default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256", "appb2048"],
@@ -232,14 +236,16 @@ def run_ours(args):
     src = torch.from_numpy(c["src"]).to(dev)
     g = torch.from_numpy(c["g"]).to(dev)
     ctx = api.Context.get(local)
-    tile = {"band": args.band, "block": args.block, "variant": args.variant, "autotuned": False}
-    if not (args.band and args.block and args.variant):
+    tile = {"band": args.band, "block": args.block, "variant": args.variant, "window": args.window,
+            "autotuned": False}
+    if not args.variant:
         from paper_2603_00035_gb300 import autotune
         proj0, _ = api.rf_project(raw, eps, delta)
-        b_, k_, n_ = autotune.tune_sweep(proj0, eps, src, h)
-        tile = {"band": b_, "block": k_, "variant": n_, "autotuned": True, "cache": autotune.cache_path()}
+        b_, k_, n_, w_ = autotune.tune_sweep(proj0, eps, src, h)
+        tile = {"band": b_, "block": k_, "variant": n_, "window": w_, "autotuned": True,
+                "cache": autotune.cache_path()}
         del proj0
-    opts = api.make_opts(band=tile["band"], block=tile["block"], variant=tile["variant"])
+    opts = api.make_opts(band=tile["band"], block=tile["block"], variant=tile["variant"], window=tile["window"])
     stream = torch.cuda.current_stream()
     # preallocated outputs: the timed steps allocate nothing
     proj = torch.empty_like(raw)
@@ -358,7 +364,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": dict(workload_config(n), tile=tile),
             "roofline": roofline, "e2e": e2e,
-            "gpu_launches": (LAUNCHES_PER_STEP[args.algo] + (tile["variant"] in (0, STREAMED))) * args.steps,
+            "gpu_launches": (LAUNCHES_BASE + LAUNCHES_FORWARD[tile["variant"] or 8] + LAUNCHES_ADJOINT[args.algo]) *
+                            args.steps,
             "clocks": sampler.summary(),
             "solver": {"sweeps": sweeps, "adj_sweeps": adj_sweeps, "cell_updates": cell_updates,
                        "gcell_updates_per_s": cell_updates / (phase_ms[1] / 1e3) / 1e9,

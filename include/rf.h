@@ -76,9 +76,9 @@ enum rf_adjoint_algo {
  *            node, two-point candidates in the cone form (same values up to
  *            FP32 rounding);
  *  TILED4    as TILED1 with four threads per node and a shuffle minimum;
- *  TILES     tile queue: 32 x 32 tiles iterated (Jacobi, one thread per
- *            node, constants in registers) to a local fixed point with
- *            their halo ring fixed; a tile whose boundary moved queues its
+ *  TILES     tile queue: 16 x 16 (or 32 x 32) tiles iterated (Jacobi, one
+ *            thread per node, four 16 x 16 tiles per 1024-thread CTA) to a
+ *            local fixed point with their halo ring fixed; a tile whose boundary moved queues its
  *            neighbours for the next round, and each round processes the
  *            queued tiles within a window of the smallest arrival time
  *            (delta-stepping); deterministic (tiles read their neighbours'
@@ -100,7 +100,8 @@ typedef struct rf_opts {
   float tol;          /* absolute part of the change test (see rtol)        */
   int32_t max_sweeps; /* cap on directional sweeps (4 per iteration)       */
   int32_t mode;       /* enum rf_mode                                       */
-  int32_t band;       /* lines per band (0 = auto)                          */
+  int32_t band;       /* line sweeps: lines per band (0 = auto); TILES:
+                         tile side, 16 or 32 (0 = 16)                     */
   int32_t block;      /* line steps per block, <= band (0 = auto)           */
   float rtol;         /* a node counts as changed in a sweep when
                          |T_new - T_old| > tol + rtol * T_new (either value
@@ -112,8 +113,8 @@ typedef struct rf_opts {
   int32_t variant;    /* enum rf_sweep_variant (0 = auto)                   */
   float window;       /* TILES: a round processes the queued tiles whose
                          key (smallest new boundary time that queued them)
-                         is within window x 32 x (mean edge cost) of the
-                         smallest key (0 = auto: 2)                        */
+                         is within window x (tile side) x (mean edge
+                         cost) of the smallest key (0 = auto: 2)           */
 } rf_opts;
 
 /* Per-node record of the converged forward solve (Alg. 2, first loop). */

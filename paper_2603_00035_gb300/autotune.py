@@ -1,13 +1,16 @@
-"""Autotuner for the line-tile shape of the forward sweep.
+"""Autotuner for the forward solve's kernel variant and tile shape.
 
-rf_sweep_forward splits every sweep's lines into bands of R lines (one CTA
-each) and advances a band K line steps per block (halo of K lines), with
-one of the kernel variants of rf_sweep_variant.  The best (R, K, variant)
-depends on the grid size and the GPU.  tune_sweep() times the candidate
-shapes on a real solve and keeps the fastest per grid-size bucket (next
-power of two of max(ny, nx)); results are cached in a JSON file keyed by
-the GPU name, so later processes reuse them without timing again.  Cache
-entries without a variant field (written before it existed) are ignored.
+A shape is (band, block, variant, window): for the line-sweep variants a
+sweep's lines are split into bands of `band` lines (one CTA each) advanced
+`block` line steps per block; for the tile queue (variant 8) `band` is the
+tile side (16 or 32) and `window` the delta-stepping window in tile
+crossings (0 = the kernel's default).  The best shape depends on the grid
+size and the GPU.  tune_sweep() times the candidate shapes on a real solve
+and keeps the fastest per grid-size bucket (next power of two of
+max(ny, nx)); results are cached in a JSON file keyed by the GPU name, so
+later processes reuse them without timing again.  Cache entries without a
+variant field (written before it existed) are ignored; entries without a
+window read as window 0.
 
 Cache file: $RF_AUTOTUNE_CACHE, else ~/.cache/rf_gb300/autotune.json.
 """
@@ -17,9 +20,10 @@ import json
 import os
 import threading
 
-# (band, block, variant): 2 streamed, 1 tiled with one thread per node, 4 tiled with four
-CANDIDATES = [(32, 32, 2), (64, 16, 2), (32, 16, 2), (16, 16, 2), (32, 32, 1), (16, 16, 1), (32, 16, 1),
-              (32, 32, 4)]
+# (band, block, variant, window): 8 tile queue (band = tile side), 2 streamed, 1 tiled with one
+# thread per node, 4 tiled with four
+CANDIDATES = [(16, 0, 8, 0.0), (16, 0, 8, 2.0), (16, 0, 8, 8.0), (32, 0, 8, 0.0), (32, 0, 8, 4.0),
+              (32, 32, 2, 0.0), (64, 16, 2, 0.0), (32, 16, 2, 0.0), (32, 32, 1, 0.0), (32, 32, 4, 0.0)]
 
 _lock = threading.Lock()
 
@@ -57,20 +61,22 @@ def _store(d: dict) -> None:
 
 
 def lookup(device_name: str, ny: int, nx: int):
-    """(band, block, variant) cached for this GPU and size bucket, or None."""
+    """(band, block, variant, window) cached for this GPU and size bucket,
+    or None."""
     with _lock:
         e = _load().get(device_name, {}).get(str(bucket(ny, nx)))
     if not e or "variant" not in e:
         return None
-    return (int(e["band"]), int(e["block"]), int(e["variant"]))
+    return (int(e["band"]), int(e["block"]), int(e["variant"]), float(e.get("window", 0.0)))
 
 
-def record(device_name: str, ny: int, nx: int, band: int, block: int, variant: int, ms: float, table=None) -> None:
+def record(device_name: str, ny: int, nx: int, band: int, block: int, variant: int, window: float, ms: float,
+           table=None) -> None:
     with _lock:
         d = _load()
         d.setdefault(device_name, {})[str(bucket(ny, nx))] = {"band": int(band), "block": int(block),
-                                                              "variant": int(variant), "ms": float(ms),
-                                                              "timings": table or {}}
+                                                              "variant": int(variant), "window": float(window),
+                                                              "ms": float(ms), "timings": table or {}}
         _store(d)
 
 
@@ -84,9 +90,9 @@ def choose(timings: dict):
 
 
 def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
-    """Time rf_sweep_forward for each candidate (band, block, variant) on this
-    input, cache and return the fastest.  Uses the cached result unless
-    force."""
+    """Time rf_sweep_forward for each candidate (band, block, variant,
+    window) on this input, cache and return the fastest.  Uses the cached
+    result unless force."""
     import torch
 
     from . import api
@@ -100,8 +106,8 @@ def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
     T = torch.empty((ny, nx), dtype=torch.float32, device=proj5.device)
     timings = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for band, block, variant in (candidates or CANDIDATES):
-        o = api.make_opts(band=band, block=block, variant=variant)
+    for band, block, variant, window in (candidates or CANDIDATES):
+        o = api.make_opts(band=band, block=block, variant=variant, window=window)
         try:
             api.rf_sweep_forward(proj5, eps, src, h, opts=o, T=T, record=False)
         except Exception:
@@ -112,10 +118,11 @@ def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
             api.rf_sweep_forward(proj5, eps, src, h, opts=o, T=T, record=False)
         e1.record()
         torch.cuda.synchronize()
-        timings[(band, block, variant)] = e0.elapsed_time(e1) / repeats
+        timings[(band, block, variant, window)] = e0.elapsed_time(e1) / repeats
     api.Context.get(proj5.device).stats()
     best = choose(timings)
-    record(name, ny, nx, *best, timings[best], {f"{b}x{k}x{n}": round(v, 4) for (b, k, n), v in timings.items()})
+    record(name, ny, nx, *best, timings[best],
+           {f"{b}x{k}x{n}x{w:g}": round(v, 4) for (b, k, n, w), v in timings.items()})
     return best
 
 
@@ -127,4 +134,5 @@ def best_opts(device_name: str, ny: int, nx: int, **kw):
         kw.setdefault("band", hit[0])
         kw.setdefault("block", hit[1])
         kw.setdefault("variant", hit[2])
+        kw.setdefault("window", hit[3])
     return api.make_opts(**kw)

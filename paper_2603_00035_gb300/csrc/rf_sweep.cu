@@ -539,7 +539,8 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
 
   // tile queue: the default when its workspace can be allocated
   if (o.variant == RF_SWEEP_TILES || o.variant == RF_SWEEP_AUTO) {
-    rf_status rt = ensure(&ctx->tilebuf, &ctx->tilebuf_cap, rf::tile_work_bytes(ny, nx));
+    const int ts = rf::tile_side(o.variant == RF_SWEEP_TILES ? o.band : 0);
+    rf_status rt = ensure(&ctx->tilebuf, &ctx->tilebuf_cap, rf::tile_work_bytes(ny, nx, ts));
     if (rt == RF_OK) rt = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)n);
     if (rt == RF_OK) rt = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2);
     if (rt != RF_OK && o.variant == RF_SWEEP_TILES) return rt;
@@ -556,8 +557,8 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
       ctl.st = ctx->state;
       ctl.abort = ctx->changed + o.max_sweeps + 1;
       ctl.timeout_ns = ctx->timeout_ns;
-      const rf::TileWork w = rf::tile_work_carve(ctx->tilebuf, ny, nx);
-      rt = rf::tiles_launch(ctx->device, ctx->num_sms, ny, nx, grid->h, eps, proj5, src, T, ctx->tbuf,
+      const rf::TileWork w = rf::tile_work_carve(ctx->tilebuf, ny, nx, ts);
+      rt = rf::tiles_launch(ctx->num_sms, ny, nx, ts, grid->h, eps, proj5, src, T, ctx->tbuf,
                             o.mode == RF_MODE_WARM, o.max_sweeps, o.tol, o.rtol, o.window, w, ctl, s);
       if (rt != RF_OK) return rt;
       if (rec) {

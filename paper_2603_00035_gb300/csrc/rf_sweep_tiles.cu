@@ -5,16 +5,19 @@
 // candidates (replacement update), and the solve stops at a state where no
 // node would change by more than tol + rtol T.  Only the schedule differs.
 // The paper's column/row fronts need one dependent step per grid line and
-// per sweep (2048 x 15 at 2048^2); here the grid is cut into 32 x 32 tiles
-// and the work is organised in rounds:
+// per sweep (2048 x 15 at 2048^2); here the grid is cut into square tiles
+// (16 x 16 by default, or 32 x 32) and the work is organised in rounds:
 //
-//  * a round processes the tiles in its queue; a processed tile loads its
-//    nodes' cone-form constants (rf_cone.cuh) into registers -- one thread
-//    per node -- and its current T plus a one-node halo ring into shared
-//    memory, then iterates Jacobi updates with the halo held fixed until no
-//    node changes (a local fixed point).  A warp owns an 8 x 4 patch and
-//    only evaluates when a node next to one of its nodes changed in the
-//    previous iteration (per-row change masks, one byte per warp and row);
+//  * a round processes the tiles in its queue.  A CTA of 1024 threads runs
+//    1024 / tile-nodes independent tile groups (one thread per node, a named
+//    barrier per group), so four 16 x 16 tiles iterate side by side on an
+//    SM.  A processed tile computes its nodes' cone-form constants
+//    (rf_cone.cuh) into shared memory and loads its current T plus a
+//    one-node halo ring, then iterates Jacobi updates with the halo held
+//    fixed until no node changes (a local fixed point).  A warp owns an
+//    8 x 4 patch and only evaluates when a node next to one of its nodes
+//    changed in the previous iteration (per-row change masks, one byte per
+//    warp and row);
 //  * a tile whose boundary nodes changed queues its neighbours for the next
 //    round, keyed by the smallest new boundary time; a round processes the
 //    queued tiles whose key is within a window of the smallest key and
@@ -23,11 +26,15 @@
 //  * tiles read their neighbours' state as of the start of the round: every
 //    tile's latest version lives in one of two T buffers, tagged per tile
 //    with (round written, parity); a tile writes its new version into the
-//    other buffer, so results do not depend on the order in which the CTAs
-//    take tiles, and the solve is deterministic;
-//  * the solve ends when a round queues nothing: every tile then sits at a
-//    local fixed point of an unchanged halo, i.e. the whole grid is a fixed
-//    point of T = min valid candidate(T) to the change tolerance.
+//    other buffer, so results do not depend on the order in which tiles are
+//    taken, and the solve is deterministic;
+//  * when a round queues nothing, the next round certifies: it visits every
+//    tile with every node marked changed, so each node is evaluated once with
+//    the current values (a change below the tolerance never marks its
+//    neighbours, so such changes could otherwise add up); the solve ends
+//    after a certification round in which no tile moved -- every node is
+//    then within tol + rtol T of min valid candidate(T), the guarantee of
+//    the line sweeps' final no-change sweep.
 //
 // The dependent chain is the number of Jacobi iterations along the path of
 // the front (a few thousand at 2048^2) instead of sweeps x grid lines.
@@ -40,14 +47,9 @@
 
 namespace rf {
 
-constexpr int kTS = 32;              // tile side in nodes
-constexpr int kTW = kTS + 2;         // tile side with the halo ring
-constexpr int kHalo = 4 * kTS + 4;   // halo ring nodes
-constexpr int kTP = kTW + 6;         // shared-memory row pitch: rows 8 banks apart, so the
-                                     // 4 rows x 8 columns of a warp's patch hit 32 banks
-constexpr int kTileThreads = kTS * kTS;
+constexpr int kTileCta = 1024;     // threads per CTA (one or four tile groups)
 constexpr unsigned kInfBits = 0x7f800000u;
-constexpr int kSlots = 3;            // list / counter slots (round mod 3)
+constexpr int kSlots = 3;          // list / counter slots (round mod 3)
 
 // control words of one round slot
 struct TileSlot {
@@ -56,9 +58,39 @@ struct TileSlot {
   unsigned kmin;   // float bits of the smallest queued key
   unsigned pad;
 };
+// ctrl layout (unsigned words): 3 slots x 4, mean edge cost, its sum, tiles
+// that published a new version [3] (by round mod 3)
+constexpr int kCtrlEbar = kSlots * 4;
+constexpr int kCtrlEsum = kCtrlEbar + 1;
+constexpr int kCtrlMoved = kCtrlEbar + 2;
+
+template <int TS>
+struct TileGeom {
+  static constexpr int TW = TS + 2;              // tile side with the halo ring
+  static constexpr int HALO = 4 * TS + 4;        // halo ring nodes
+  static constexpr int NODES = TS * TS;          // threads per group
+  static constexpr int GROUPS = kTileCta / NODES;
+  static constexpr int TP = (TS == 32) ? 40 : 24;  // row pitch: rows 8 banks apart, so
+                                                   // a warp's 4 x 8 patch hits 32 banks
+  static constexpr int PCOLS = TS / 8;           // 8-column patches per row of patches
+  static_assert(TS == 16 || TS == 32, "tile side");
+  static_assert(GROUPS * NODES == kTileCta, "groups fill the CTA");
+};
+
+// Shared memory of one tile group.
+template <int TS>
+struct alignas(16) GroupSmem {
+  float4 q[kPlanes][TileGeom<TS>::NODES];                  // cone-form constants per node
+  float Ts[2][TileGeom<TS>::TW][TileGeom<TS>::TP];         // T, double-buffered, with halo
+  unsigned long long rowm[2][TileGeom<TS>::TW];            // change masks (see colspace)
+  unsigned nkey[9];                                        // smallest changed boundary time per neighbour
+  int par[9];                                              // round-start buffer of the 3 x 3 tiles
+  int tile, go, first;
+  unsigned key;
+};
 
 struct TileArgs {
-  int ny, nx, tny, tnx, ntiles;
+  int ny, nx, ts, tny, tnx, ntiles;
   float h, eps;
   const float *f;
   const uint8_t *src;
@@ -71,26 +103,47 @@ struct TileArgs {
   LaunchCtl ctl;
 };
 
-// Halo index -> (row, column) in the (kTW x kTW) tile frame.
-__device__ __forceinline__ void halo_rc(int k, int &r, int &c) {
-  if (k < kTW) { r = 0; c = k; }
-  else if (k < 2 * kTW) { r = kTW - 1; c = k - kTW; }
-  else if (k < 2 * kTW + kTS) { r = 1 + (k - 2 * kTW); c = 0; }
-  else { r = 1 + (k - 2 * kTW - kTS); c = kTW - 1; }
+// Named barrier of a tile group (ids 1..4; 0 is __syncthreads).
+template <int N>
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ int group_sync_or(int id, int pred) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.s32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(pred), "r"(id), "n"(N)
+      : "memory");
+  return r;
 }
 
-// Change masks: one 64-bit word per frame row; bits 0..31 are the interior
-// columns 0..31 (byte k written by the warps of patch column k), bit 32 the
-// left halo column, bit 33 the right one.  colspace() maps a word to frame
-// column order (bit c = frame column c, 0..33).
+// Change masks: one 64-bit word per frame row; bits 0..TS-1 are the interior
+// columns (byte k written by the warps of patch column k), bit TS the left
+// halo column, bit TS+1 the right one.  colspace() maps a word to frame
+// column order (bit c = frame column c).
+template <int TS>
 __device__ __forceinline__ unsigned long long colspace(unsigned long long w) {
-  return ((w & 0xffffffffull) << 1) | ((w >> 32) & 1ull) | (((w >> 33) & 1ull) << 33);
+  constexpr unsigned long long lo = (1ull << TS) - 1ull;
+  return ((w & lo) << 1) | ((w >> TS) & 1ull) | (((w >> (TS + 1)) & 1ull) << (TS + 1));
 }
+template <int TS>
 __device__ __forceinline__ unsigned long long frame_bit(int c) {
-  return c == 0 ? (1ull << 32) : (c == kTW - 1) ? (1ull << 33) : (1ull << (c - 1));
+  return c == 0 ? (1ull << TS) : (c == TS + 1) ? (1ull << (TS + 1)) : (1ull << (c - 1));
 }
 
-// Buffer holding tile t's version as of the start of round r.
+// Halo index -> (row, column) in the tile frame.
+template <int TS>
+__device__ __forceinline__ void halo_rc(int k, int &r, int &c) {
+  constexpr int TW = TS + 2;
+  if (k < TW) { r = 0; c = k; }
+  else if (k < 2 * TW) { r = TW - 1; c = k - TW; }
+  else if (k < 2 * TW + TS) { r = 1 + (k - 2 * TW); c = 0; }
+  else { r = 1 + (k - 2 * TW - TS); c = TW - 1; }
+}
+
+// Buffer holding a tile's version as of the start of round r.
 __device__ __forceinline__ int start_parity(unsigned st, int r) {
   const int par = (int)(st & 1u);
   return ((int)(st >> 1) == r) ? 1 - par : par;
@@ -112,26 +165,31 @@ __device__ __forceinline__ void push(const TileWork &w, int ntiles, int t, int r
   enqueue(w, ntiles, t, rr);
 }
 
-__global__ void __launch_bounds__(kTileThreads, 1) tile_solve_kernel(TileArgs a) {
-  __shared__ float Ts[2][kTW][kTP];
-  __shared__ unsigned long long rowm[2][kTW];  // change masks (see colspace)
-  __shared__ unsigned nkey[9];                 // smallest changed boundary time per neighbour
-  __shared__ int s_tile, s_go, s_par[9];
-  __shared__ unsigned s_key;
-
-  // warp w owns the 8 x 4 patch (w >> 2, w & 3) of the tile
-  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  const int pr = wp >> 2, pc = wp & 3, ao = lane >> 3;
+template <int TS>
+__global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
+  using G = TileGeom<TS>;
+  constexpr int NG = G::NODES;
+  extern __shared__ float4 smem4[];
+  const int tid = threadIdx.x;
+  const int grp = tid / NG, gt = tid - grp * NG;  // group and thread within it
+  GroupSmem<TS> &S = reinterpret_cast<GroupSmem<TS> *>(smem4)[grp];
+  const int bar = 1 + grp;
+  // warp w of the group owns the 8 x 4 patch (w / PCOLS, w % PCOLS)
+  const int lane = gt & 31, wp = gt >> 5;
+  const int pr = wp / G::PCOLS, pc = wp % G::PCOLS, ao = lane >> 3;
   const int row = pr * 4 + ao, col = pc * 8 + (lane & 7);
+  const int sr = row + 1, sc = col + 1;
+
   const TileWork &w = a.w;
   const int NT = a.ntiles;
   const long long plane = (long long)a.ny * a.nx;
   TileSlot *slots = reinterpret_cast<TileSlot *>(w.ctrl);
+  unsigned *moved_ct = w.ctrl + kCtrlMoved;
   unsigned long long my_updates = 0, my_warp_evals = 0;
-  bool converged = false, abort = false;
+  bool converged = false, abort = false, prev_cert = false;
   int r = 1;
-  const float ebar = __uint_as_float(w.ctrl[kSlots * 4]);  // mean edge cost (seed kernel)
-  const float delta = a.window * (float)kTS * ebar;
+  const float ebar = __uint_as_float(w.ctrl[kCtrlEbar]);  // mean edge cost (seed kernel)
+  const float delta = a.window * (float)TS * ebar;
 
   for (;; ++r) {
     TileSlot *cur = slots + (r % kSlots);
@@ -141,143 +199,167 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_solve_kernel(TileArgs a)
       old->count = 0;
       old->grab = 0;
       old->kmin = kInfBits;
+      // round r - 2's moved count was read at the start of round r - 1
+      moved_ct[(r + 1) % kSlots] = 0u;
     }
-    const unsigned n = __ldcg(&cur->count);
-    if (n == 0) {
-      converged = true;
-      break;
+    unsigned n = __ldcg(&cur->count);
+    // an empty queue: done if the previous round certified without a change,
+    // else certify (every tile, every node evaluated)
+    const bool cert = n == 0;
+    if (cert) {
+      if (prev_cert && __ldcg(&moved_ct[(r + 2) % kSlots]) == 0u) {
+        converged = true;
+        break;
+      }
+      n = (unsigned)NT;
     }
+    prev_cert = cert;
     if (r > a.max_rounds) break;
-    const float theta = __uint_as_float(__ldcg(&cur->kmin)) + delta;
+    const float theta = cert ? kInf : __uint_as_float(__ldcg(&cur->kmin)) + delta;
+
     while (true) {
-      if (tid == 0) {
+      if (gt == 0) {
         const unsigned k = atomicAdd(&cur->grab, 1u);
-        s_go = k < n;
-        if (k < n) {
+        S.go = k < n;
+        if (k < n && cert) {
+          S.tile = (int)k;
+          S.key = 0u;
+        } else if (k < n) {
           const int t = __ldcg(&w.list[(size_t)(r % kSlots) * NT + k]);
-          s_tile = t;
+          S.tile = t;
           unsigned *kp = &w.key[(size_t)(r & 1) * NT + t];
-          s_key = __ldcg(kp);
+          S.key = __ldcg(kp);
           __stcg(kp, kInfBits);
         }
       }
-      __syncthreads();
-      if (!s_go) break;
-      const int t = s_tile;
-      const unsigned kb = s_key;
+      group_sync<NG>(bar);
+      if (!S.go) break;
+      const int t = S.tile;
+      const unsigned kb = S.key;
       if (__uint_as_float(kb) > theta) {
         // too far ahead of the front: keep it for a later round
-        if (tid == 0) push(w, NT, t, r + 1, kb);
-        __syncthreads();
+        if (gt == 0) push(w, NT, t, r + 1, kb);
+        group_sync<NG>(bar);
         continue;
       }
       const int ti = t / a.tnx, tj = t - ti * a.tnx;
-      const int i0 = ti * kTS, j0 = tj * kTS;
-      // buffer parities of this tile and its eight neighbours as of the
-      // round's start (index (di + 1) * 3 + (dj + 1))
-      if (tid < 9) {
-        const int di = tid / 3 - 1, dj = tid % 3 - 1;
-        const int ni = ti + di, nj = tj + dj;
-        int p = 0;
-        if (ni >= 0 && ni < a.tny && nj >= 0 && nj < a.tnx)
-          p = start_parity(__ldcg(&w.tstate[ni * a.tnx + nj]), r);
-        s_par[tid] = p;
-        nkey[tid] = kInfBits;
-      }
-      if (tid < kTW) {
-        rowm[0][tid] = 0ull;
-        rowm[1][tid] = 0ull;
-      }
-      __syncthreads();
-      const int pt = s_par[4];
-      const float *Tin = a.T[pt];
-      float *Tout = a.T[1 - pt];
-      // this thread's node and its cone-form constants
+      const int i0 = ti * TS, j0 = tj * TS;
+      // Everything that does not depend on the neighbours' buffer parities is
+      // requested first, so that a visit pays two dependent global round
+      // trips (parities, then T) instead of one per step.
       const int i = i0 + row, j = j0 + col;
       const bool inb = (i < a.ny) && (j < a.nx);
       const long long p = (long long)i * a.nx + j;
-      float4 q[kPlanes];
+      float fl[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       bool is_src = false;
-      float tcur = kInf;
       if (inb) {
-        is_src = a.src[p] != 0;
-        node_record(__ldg(a.f + p), __ldg(a.f + plane + p), __ldg(a.f + 2 * plane + p), __ldg(a.f + 3 * plane + p),
-                    __ldg(a.f + 4 * plane + p), a.h, a.eps, is_src, q);
-        tcur = __ldcg(Tin + p);
-      } else {
 #pragma unroll
-        for (int c = 0; c < kPlanes; ++c) q[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < 5; ++c) fl[c] = __ldg(a.f + c * plane + p);
+        is_src = a.src[p] != 0;
+      }
+      int hr = 0, hc = 0, gi = -1, gj = -1;
+      float prev = kInf;
+      float *hp = nullptr;
+      if (gt < G::HALO) {
+        halo_rc<TS>(gt, hr, hc);
+        gi = i0 - 1 + hr;
+        gj = j0 - 1 + hc;
+        hp = w.halo + (size_t)t * G::HALO + gt;
+        prev = __ldcg(hp);
+      }
+      // buffer parities of this tile and its eight neighbours as of the
+      // round's start (index (di + 1) * 3 + (dj + 1)); the first-visit flag
+      if (gt < 9) {
+        const int di = gt / 3 - 1, dj = gt % 3 - 1;
+        const int ni = ti + di, nj = tj + dj;
+        int pp = 0;
+        if (ni >= 0 && ni < a.tny && nj >= 0 && nj < a.tnx)
+          pp = start_parity(__ldcg(&w.tstate[ni * a.tnx + nj]), r);
+        S.par[gt] = pp;
+        S.nkey[gt] = kInfBits;
+      }
+      if (gt == 9) S.first = __ldcg(&w.visits[t]) == 0u;
+      if (gt < G::TW) {
+        S.rowm[0][gt] = 0ull;
+        S.rowm[1][gt] = 0ull;
+      }
+      // this thread's node: cone-form constants into shared memory
+      if (inb) {
+        float4 q[kPlanes];
+        node_record(fl[0], fl[1], fl[2], fl[3], fl[4], a.h, a.eps, is_src, q);
+#pragma unroll
+        for (int c = 0; c < kPlanes; ++c) S.q[c][gt] = q[c];
+      }
+      group_sync<NG>(bar);
+      const int pt = S.par[4];
+      float *Tout = a.T[1 - pt];
+      float tcur = inb ? __ldcg(a.T[pt] + p) : kInf;
+      // halo ring, from the neighbours' round-start versions; nodes whose
+      // value differs from this tile's previous visit seed the change masks
+      if (gt < G::HALO) {
+        float v = kInf;
+        if (gi >= 0 && gi < a.ny && gj >= 0 && gj < a.nx) {
+          const int di = (hr == 0) ? -1 : (hr == G::TW - 1) ? 1 : 0;
+          const int dj = (hc == 0) ? -1 : (hc == G::TW - 1) ? 1 : 0;
+          v = __ldcg(a.T[S.par[(di + 1) * 3 + dj + 1]] + (long long)gi * a.nx + gj);
+        }
+        S.Ts[0][hr][hc] = v;
+        S.Ts[1][hr][hc] = v;
+        if (node_changed(v, prev, a.tol, a.rtol)) atomicOr(&S.rowm[0][hr], frame_bit<TS>(hc));
+        __stcg(hp, v);
       }
       const bool upd = inb && !is_src;
       const float tinit = tcur;
-      Ts[0][row + 1][col + 1] = tcur;
-      Ts[1][row + 1][col + 1] = tcur;
-      // halo ring, from the neighbours' round-start versions; nodes whose
-      // value differs from this tile's previous visit seed the change masks
-      if (tid < kHalo) {
-        int hr, hc;
-        halo_rc(tid, hr, hc);
-        const int gi = i0 - 1 + hr, gj = j0 - 1 + hc;
-        float v = kInf;
-        if (gi >= 0 && gi < a.ny && gj >= 0 && gj < a.nx) {
-          const int di = (hr == 0) ? -1 : (hr == kTW - 1) ? 1 : 0;
-          const int dj = (hc == 0) ? -1 : (hc == kTW - 1) ? 1 : 0;
-          v = __ldcg(a.T[s_par[(di + 1) * 3 + dj + 1]] + (long long)gi * a.nx + gj);
-        }
-        Ts[0][hr][hc] = v;
-        Ts[1][hr][hc] = v;
-        float *hp = w.halo + (size_t)t * kHalo + tid;
-        const float prev = __ldcg(hp);
-        if (node_changed(v, prev, a.tol, a.rtol)) atomicOr(&rowm[0][hr], frame_bit(hc));
-        __stcg(hp, v);
-      }
-      // first visit: the sources (cold) or every node (warm) start changed
-      const bool first = __ldcg(&w.visits[t]) == 0u;
-      if (first) {
-        const bool seed = inb && (a.warm ? true : is_src);
+      S.Ts[0][sr][sc] = tcur;
+      S.Ts[1][sr][sc] = tcur;
+      // first visit: the sources (cold) or every node (warm) start changed;
+      // a certification visit evaluates every node
+      if (S.first || cert) {
+        const bool seed = inb && (a.warm || cert || is_src);
         const unsigned bal = __ballot_sync(0xffffffffu, seed);
         const unsigned long long byte = (bal >> (8 * ao)) & 0xffu;
-        if ((lane & 7) == 0 && byte) atomicOr(&rowm[0][row + 1], byte << (8 * pc));
+        if ((lane & 7) == 0 && byte) atomicOr(&S.rowm[0][sr], byte << (8 * pc));
       }
-      __syncthreads();
+      group_sync<NG>(bar);
 
       // Jacobi iterations with the halo fixed
       int cb = 0, it = 0;
       bool capped = false;
-      const int sr = row + 1, sc = col + 1;
       while (true) {
-        const unsigned long long nb = ((colspace(rowm[cb][sr - 1]) | colspace(rowm[cb][sr + 1])) >> (sc - 1)) & 7ull |
-                                      ((colspace(rowm[cb][sr]) >> (sc - 1)) & 5ull);
-        const bool dirty = nb != 0ull;
-        const unsigned dball = __ballot_sync(0xffffffffu, dirty && upd);
+        const unsigned long long nb =
+            ((colspace<TS>(S.rowm[cb][sr - 1]) | colspace<TS>(S.rowm[cb][sr + 1])) >> (sc - 1)) & 7ull |
+            ((colspace<TS>(S.rowm[cb][sr]) >> (sc - 1)) & 5ull);
+        const unsigned dball = __ballot_sync(0xffffffffu, nb != 0ull && upd);
         float tnew = tcur;
         if (dball) {
           if (upd) {
             float Tn[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) Tn[k] = Ts[cb][sr + nb_dy(k)][sc + nb_dx(k)];
-            tnew = cone_min(q[0], q[1], q[2], q[3], q[4], q[5], Tn);
+            for (int k = 0; k < 8; ++k) Tn[k] = S.Ts[cb][sr + nb_dy(k)][sc + nb_dx(k)];
+            tnew = cone_min(S.q[0][gt], S.q[1][gt], S.q[2][gt], S.q[3][gt], S.q[4][gt], S.q[5][gt], Tn);
           }
           if (lane == 0) {
             my_updates += (unsigned long long)__popc(dball);
             my_warp_evals += 1;
           }
         }
-        Ts[cb ^ 1][sr][sc] = tnew;
+        S.Ts[cb ^ 1][sr][sc] = tnew;
         const bool ch = upd && node_changed(tnew, tcur, a.tol, a.rtol);
         const unsigned cbal = __ballot_sync(0xffffffffu, ch);
         // this warp's byte of each of its four rows (plain byte stores: the
-        // four patch columns of a row write disjoint bytes)
+        // patch columns of a row write disjoint bytes)
         if ((lane & 7) == 0)
-          reinterpret_cast<unsigned char *>(&rowm[cb ^ 1][sr])[pc] = (unsigned char)((cbal >> (8 * ao)) & 0xffu);
+          reinterpret_cast<unsigned char *>(&S.rowm[cb ^ 1][sr])[pc] = (unsigned char)((cbal >> (8 * ao)) & 0xffu);
         // slot 0 still holds the initial halo bits, read only by iteration 0:
-        // clear them before iteration 2 reads the slot again
-        if (it == 1 && tid < kTW) {
-          reinterpret_cast<unsigned *>(&rowm[0][tid])[1] = 0u;
-          if (tid == 0 || tid == kTW - 1) reinterpret_cast<unsigned *>(&rowm[0][tid])[0] = 0u;
+        // clear them before iteration 2 reads the slot again (the halo bytes
+        // of interior rows; halo rows entirely)
+        if (it == 1 && gt < G::TW) {
+          unsigned char *bytes = reinterpret_cast<unsigned char *>(&S.rowm[0][gt]);
+          const int from = (gt == 0 || gt == G::TW - 1) ? 0 : TS / 8;
+          for (int b = from; b < 8; ++b) bytes[b] = 0;
         }
         tcur = tnew;
-        const int any = __syncthreads_or(ch);
+        const int any = group_sync_or<NG>(bar, ch);
         cb ^= 1;
         ++it;
         if (!any) break;
@@ -289,35 +371,38 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_solve_kernel(TileArgs a)
 
       // publish: a new version only if some node moved beyond the tolerance
       const bool moved = upd && node_changed(tcur, tinit, a.tol, a.rtol);
-      if (__syncthreads_or(moved)) {
+      if (group_sync_or<NG>(bar, moved)) {
         if (inb) __stcg(Tout + p, tcur);
         if (moved) {
           const unsigned kbits = __float_as_uint(tcur);
-          const bool top = row == 0, bot = row == kTS - 1, lft = col == 0, rgt = col == kTS - 1;
-          if (top) atomicMin(&nkey[1], kbits);
-          if (bot) atomicMin(&nkey[7], kbits);
-          if (lft) atomicMin(&nkey[3], kbits);
-          if (rgt) atomicMin(&nkey[5], kbits);
-          if (top && lft) atomicMin(&nkey[0], kbits);
-          if (top && rgt) atomicMin(&nkey[2], kbits);
-          if (bot && lft) atomicMin(&nkey[6], kbits);
-          if (bot && rgt) atomicMin(&nkey[8], kbits);
+          const bool top = row == 0, bot = row == TS - 1, lft = col == 0, rgt = col == TS - 1;
+          if (top) atomicMin(&S.nkey[1], kbits);
+          if (bot) atomicMin(&S.nkey[7], kbits);
+          if (lft) atomicMin(&S.nkey[3], kbits);
+          if (rgt) atomicMin(&S.nkey[5], kbits);
+          if (top && lft) atomicMin(&S.nkey[0], kbits);
+          if (top && rgt) atomicMin(&S.nkey[2], kbits);
+          if (bot && lft) atomicMin(&S.nkey[6], kbits);
+          if (bot && rgt) atomicMin(&S.nkey[8], kbits);
         }
-        __syncthreads();
-        if (tid == 0) __stcg(&w.tstate[t], ((unsigned)r << 1) | (unsigned)(1 - pt));
-        if (tid < 9 && tid != 4 && nkey[tid] != kInfBits) {
-          const int ni = ti + tid / 3 - 1, nj = tj + tid % 3 - 1;
-          if (ni >= 0 && ni < a.tny && nj >= 0 && nj < a.tnx) push(w, NT, ni * a.tnx + nj, r + 1, nkey[tid]);
+        group_sync<NG>(bar);
+        if (gt == 0) {
+          __stcg(&w.tstate[t], ((unsigned)r << 1) | (unsigned)(1 - pt));
+          atomicAdd(&moved_ct[r % kSlots], 1u);
+        }
+        if (gt < 9 && gt != 4 && S.nkey[gt] != kInfBits) {
+          const int ni = ti + gt / 3 - 1, nj = tj + gt % 3 - 1;
+          if (ni >= 0 && ni < a.tny && nj >= 0 && nj < a.tnx) push(w, NT, ni * a.tnx + nj, r + 1, S.nkey[gt]);
         }
       }
-      if (tid == 0) {
+      if (gt == 0) {
         __stcg(&w.visits[t], __ldcg(&w.visits[t]) + 1u);
         // a visit cut short by the iteration cap is resumed next round
         if (capped) push(w, NT, t, r + 1, kb);
       }
-      __syncthreads();
+      group_sync<NG>(bar);
     }
-    if (!grid_sync(a.ctl)) {
+    if (!grid_sync(a.ctl)) {  // begins with __syncthreads: every group is done
       abort = true;
       break;
     }
@@ -328,14 +413,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_solve_kernel(TileArgs a)
   }
   if (!abort) {
     // hand the latest version of every tile back in the caller's buffer
-    for (int t = blockIdx.x; t < NT; t += gridDim.x) {
-      if ((__ldcg(&w.tstate[t]) & 1u) == 0u) continue;
-      const int ti = t / a.tnx, tj = t - ti * a.tnx;
-      const int i = ti * kTS + row, j = tj * kTS + col;
-      if (i < a.ny && j < a.nx) {
-        const long long p = (long long)i * a.nx + j;
-        a.T[0][p] = __ldcg(a.T[1] + p);
-      }
+    for (long long q = (long long)blockIdx.x * blockDim.x + tid; q < plane; q += (long long)gridDim.x * blockDim.x) {
+      const int qi = (int)(q / a.nx), qj = (int)(q - (long long)qi * a.nx);
+      if (__ldcg(&w.tstate[(qi / TS) * a.tnx + qj / TS]) & 1u) a.T[0][q] = __ldcg(a.T[1] + q);
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
@@ -345,12 +425,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_solve_kernel(TileArgs a)
   }
 }
 
-// Workspace reset and the first round's queue: the tiles holding a source
-// (cold) or every tile (warm), key 0; the mean edge cost of the field
-// (mean of (|m_x|_M + |m_y|_M) / 2) for the delta-stepping window.
+// Workspace reset and the mean edge cost of the field (mean of
+// (|m_x|_M + |m_y|_M) / 2, the time scale of the delta-stepping window).
 __global__ void tile_seed_kernel(TileArgs a, float *esum) {
   const TileWork &w = a.w;
   const int NT = a.ntiles;
+  const int halo = 4 * a.ts + 4;
   const long long plane = (long long)a.ny * a.nx;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,10 +447,9 @@ __global__ void tile_seed_kernel(TileArgs a, float *esum) {
     w.visits[t] = 0u;
     w.key[t] = kInfBits;
     w.key[NT + t] = kInfBits;
-    w.queued[t] = 0u;
-    if (a.warm) w.queued[t] = 1u;
+    w.queued[t] = a.warm ? 1u : 0u;
   }
-  for (long long k = g0; k < (long long)NT * kHalo; k += stride) w.halo[k] = kInf;
+  for (long long k = g0; k < (long long)NT * halo; k += stride) w.halo[k] = kInf;
   float part = 0.0f;
   for (long long p = g0; p < plane; p += stride) {
     const float l11 = a.f[p], l21 = a.f[plane + p], l22 = a.f[2 * plane + p];
@@ -383,7 +462,9 @@ __global__ void tile_seed_kernel(TileArgs a, float *esum) {
 }
 
 // Queue the first round (runs after tile_seed_kernel), key 0: every tile
-// (warm) or the tiles around the sources (cold).
+// (warm) or every tile that holds a source or one of its neighbours (cold: a
+// source never changes, so the tiles across a tile edge next to it must see
+// it in their halo on their own first visit).
 __global__ void tile_queue_kernel(TileArgs a) {
   const TileWork &w = a.w;
   const int NT = a.ntiles;
@@ -396,9 +477,6 @@ __global__ void tile_queue_kernel(TileArgs a) {
     }
     return;
   }
-  // every tile that holds a source or one of its neighbours: a source never
-  // changes, so the tiles across a tile edge next to it must see it in
-  // their halo on their own first visit
   const long long plane = (long long)a.ny * a.nx;
   for (long long p = g0; p < plane; p += stride) {
     if (!a.src[p]) continue;
@@ -407,7 +485,7 @@ __global__ void tile_queue_kernel(TileArgs a) {
       for (int dj = -1; dj <= 1; ++dj) {
         const int ii = i + di, jj = j + dj;
         if (ii < 0 || ii >= a.ny || jj < 0 || jj >= a.nx) continue;
-        const int t = (ii / kTS) * a.tnx + jj / kTS;
+        const int t = (ii / a.ts) * a.tnx + jj / a.ts;
         atomicMin(&w.key[NT + t], 0u);
         enqueue(w, NT, t, 1);
       }
@@ -420,7 +498,7 @@ __global__ void tile_finish_seed_kernel(TileArgs a, const float *esum) {
   if (a.warm) slots[1 % kSlots].count = (unsigned)a.ntiles;
   slots[1 % kSlots].kmin = 0u;
   const float ebar = *esum / (float)((long long)a.ny * a.nx);
-  a.w.ctrl[kSlots * 4] = __float_as_uint(ebar > 0.0f && ebar < kInf ? ebar : 1.0f);
+  a.w.ctrl[kCtrlEbar] = __float_as_uint(ebar > 0.0f && ebar < kInf ? ebar : 1.0f);
 }
 
 // Statistics of the solve: node updates and their sweep equivalent.
@@ -435,16 +513,18 @@ __global__ void tile_stats_kernel(const unsigned long long *counters, DevState *
 
 namespace rf {
 
-int tiles_count(int ny, int nx) { return ((ny + kTS - 1) / kTS) * ((nx + kTS - 1) / kTS); }
+int tile_side(int requested) { return requested >= 32 ? 32 : 16; }
 
-size_t tile_work_bytes(int ny, int nx) {
-  const size_t NT = (size_t)tiles_count(ny, nx);
-  // tstate, visits, queued, key[2], list[3], halo, ctrl, counters
-  return NT * 4 * 5 + NT * 4 * kSlots + NT * kHalo * 4 + 256 + 64;
+int tiles_count(int ny, int nx, int ts) { return ((ny + ts - 1) / ts) * ((nx + ts - 1) / ts); }
+
+size_t tile_work_bytes(int ny, int nx, int ts) {
+  const size_t NT = (size_t)tiles_count(ny, nx, ts);
+  // counters, ctrl, then tstate, visits, queued, key[2], list[3], halo
+  return 64 + 256 + NT * 4 * 5 + NT * 4 * kSlots + NT * (size_t)(4 * ts + 4) * 4;
 }
 
-TileWork tile_work_carve(void *base, int ny, int nx) {
-  const size_t NT = (size_t)tiles_count(ny, nx);
+TileWork tile_work_carve(void *base, int ny, int nx, int ts) {
+  const size_t NT = (size_t)tiles_count(ny, nx, ts);
   unsigned char *b = (unsigned char *)base;
   TileWork w;
   w.counters = (unsigned long long *)b;  // 8-byte aligned first
@@ -465,14 +545,30 @@ TileWork tile_work_carve(void *base, int ny, int nx) {
   return w;
 }
 
-rf_status tiles_launch(int device, int num_sms, int ny, int nx, float h, float eps, const float *proj5,
+template <int TS>
+static rf_status launch_solve(TileArgs &a, int num_sms, cudaStream_t s) {
+  const size_t smem = sizeof(GroupSmem<TS>) * TileGeom<TS>::GROUPS;
+  if (cudaFuncSetAttribute(tile_solve_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return RF_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_solve_kernel<TS>, kTileCta, smem) != cudaSuccess)
+    return RF_ERR_CUDA;
+  if (per_sm < 1) return RF_ERR_UNSUPPORTED;
+  void *args[] = {&a};
+  return cuda_status(cudaLaunchCooperativeKernel((const void *)tile_solve_kernel<TS>, dim3(per_sm * num_sms),
+                                                 dim3(kTileCta), args, smem, s));
+}
+
+rf_status tiles_launch(int num_sms, int ny, int nx, int ts, float h, float eps, const float *proj5,
                        const uint8_t *src, float *T, float *Tb, int warm, int max_sweeps, float tol, float rtol,
                        float window, const TileWork &w, const LaunchCtl &ctl, cudaStream_t s) {
   TileArgs a;
   a.ny = ny;
   a.nx = nx;
-  a.tny = (ny + kTS - 1) / kTS;
-  a.tnx = (nx + kTS - 1) / kTS;
+  a.ts = ts;
+  a.tny = (ny + ts - 1) / ts;
+  a.tnx = (nx + ts - 1) / ts;
   a.ntiles = a.tny * a.tnx;
   a.h = h;
   a.eps = eps;
@@ -482,30 +578,22 @@ rf_status tiles_launch(int device, int num_sms, int ny, int nx, float h, float e
   a.T[1] = Tb;
   a.tol = tol;
   a.rtol = rtol;
-  a.window = window > 0.0f ? window : 2.0f;
+  a.window = window > 0.0f ? window : (ts == 32 ? 2.0f : 4.0f);
   a.warm = warm;
   // a sweep moves information across the grid, a round across one tile
   a.max_rounds = max_sweeps * std::max(a.tny, a.tnx);
-  a.max_local = 16 * kTS;
+  a.max_local = 16 * ts;
   a.w = w;
   a.ctl = ctl;
   if (cudaMemsetAsync(w.counters, 0, 64 + 256, s) != cudaSuccess) return RF_ERR_CUDA;
-  float *esum = (float *)(w.ctrl + kSlots * 4 + 1);
+  float *esum = (float *)(w.ctrl + kCtrlEsum);
   const long long n = (long long)ny * nx;
-  const int blocks = blocks_for(std::max(n, (long long)a.ntiles * kHalo), 256, num_sms * 8);
+  const int blocks = blocks_for(std::max(n, (long long)a.ntiles * (4 * ts + 4)), 256, num_sms * 8);
   tile_seed_kernel<<<blocks, 256, 0, s>>>(a, esum);
   tile_queue_kernel<<<blocks, 256, 0, s>>>(a);
   tile_finish_seed_kernel<<<1, 32, 0, s>>>(a, esum);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_solve_kernel, kTileThreads, 0) != cudaSuccess)
-    return RF_ERR_CUDA;
-  if (per_sm < 1) return RF_ERR_UNSUPPORTED;
-  const int grid = per_sm * num_sms;
-  void *args[] = {&a};
-  (void)device;
-  if (cudaLaunchCooperativeKernel((const void *)tile_solve_kernel, dim3(grid), dim3(kTileThreads), args, 0, s) !=
-      cudaSuccess)
-    return RF_ERR_CUDA;
+  const rf_status rs = ts == 32 ? launch_solve<32>(a, num_sms, s) : launch_solve<16>(a, num_sms, s);
+  if (rs != RF_OK) return rs;
   tile_stats_kernel<<<1, 32, 0, s>>>(w.counters, ctl.st, n);
   return cuda_status(cudaGetLastError());
 }

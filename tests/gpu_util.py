@@ -8,8 +8,10 @@ Tolerances (the parity bar):
 * gradients: relative L2 <= 1e-3 over nodes outside the flip set;
 * stencils are compared in canonical form: a two-point update whose donor
   weight is within DEGENERATE of 1 (or 0) is the one-point update through its
-  first (second) donor -- same value, same partials to that order -- so the
-  two namings of one update are not a mismatch;
+  first (second) donor -- same value to second order, same partials to first
+  order -- so the two namings of one update are not a mismatch (FP32 errors
+  of ~1e-6 T in the donor times move a barycentric weight by ~1e-6 T / (h
+  |m|_M), a few 1e-4 at 1024^2, hence DEGENERATE = 1e-3);
 * near-tie: the oracle's best-vs-second valid candidate margin is
   < 1e-5 * max T (FP32 may legitimately pick either candidate there);
 * flip set: nodes whose canonical stencils differ; every flip must be a
@@ -28,7 +30,7 @@ from paper_2603_00035_gb300 import build as B  # noqa: E402
 FWD_TOL = 1e-4
 GRAD_TOL = 1e-3
 FLIP_MARGIN = 1e-5
-DEGENERATE = 1e-4
+DEGENERATE = 1e-3
 
 
 def require_gpu():
