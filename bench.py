@@ -35,6 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "forward+adjoint solves/s at 2048x2048"
 UNIT = "solves/s"
 ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-update
+# DRAM bytes (read + write) of one launch of the tile-queue forward kernel on the 2048^2 workload (16x16
+# tiles, default window), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).  Reported
+# as roofline.traffic only while the kernel's sources hash to the captured build's.
+TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048): {"sources_sha16": "68f1916a2e265cb7",
+                                                       "bytes": 308641280 + 40726528}}
+TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_00035_gb300/csrc/rf_cone.cuh"]
 # kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
 # source check, then tile queue: seed, queue, finish-seed, solve, stats; streamed: node records + sweep;
 # tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not
@@ -80,6 +86,15 @@ def workload_config(n):
             "l2": "flushed between timed steps (256 MB write)"}
 
 
+def sources_sha16(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -95,6 +110,8 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.samples = []
+        self.seen = 0
+        self.recording = False
         self._stop = threading.Event()
         self._proc = None
 
@@ -104,7 +121,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self._proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                           "--format=csv,noheader,nounits", "-lms", "20"],
                                           stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self._proc = None
@@ -113,10 +130,12 @@ class ClockSampler:
         self._t.start()
 
     def wait_first(self, timeout=5.0):
-        """Block until the first sample arrived (nvidia-smi takes a moment)."""
+        """Block until nvidia-smi delivers samples, then keep only the
+        samples taken from now on (the timed region)."""
         t0 = time.time()
-        while self._proc and not self.samples and time.time() - t0 < timeout:
+        while self._proc and not self.seen and time.time() - t0 < timeout:
             time.sleep(0.05)
+        self.recording = True
 
     def _read(self):
         for line in self._proc.stdout:
@@ -124,7 +143,9 @@ class ClockSampler:
                 break
             parts = [x.strip() for x in line.split(",")]
             if len(parts) >= 8:
-                self.samples.append(parts)
+                self.seen += 1
+                if self.recording:
+                    self.samples.append(parts)
 
     def stop(self):
         self._stop.set()
@@ -289,6 +310,7 @@ def run_ours(args):
     total_ms = 0.0
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.wait_first()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -357,6 +379,11 @@ def run_ours(args):
         bytes_per_launch = 60 * n * n
     achieved = bytes_per_launch / (phase_ms[dom] / 1e3) / 1e9
     traffic = None
+    if names[dom] == "sweep_forward" and tile["variant"] in (0, 8) and tile["band"] in (0, 16) and \
+            tile["window"] == 0.0:
+        cap = TRAFFIC_CAPTURES.get(("tile_solve_kernel<16>", n))
+        if cap and sources_sha16(TRAFFIC_SOURCES) == cap["sources_sha16"]:
+            traffic = cap["bytes"]
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic}
 
@@ -429,6 +456,7 @@ def run_batch(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.wait_first()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()

@@ -13,7 +13,10 @@ Tolerances (the parity bar):
   of ~1e-6 T in the donor times move a barycentric weight by ~1e-6 T / (h
   |m|_M), a few 1e-4 at 1024^2, hence DEGENERATE = 1e-3);
 * near-tie: the oracle's best-vs-second valid candidate margin is
-  < 1e-5 * max T (FP32 may legitimately pick either candidate there);
+  < 1e-5 * max T + 2 e, e the largest |T_gpu - T_oracle| over the node's 3 x 3
+  neighbourhood: a candidate is 1-Lipschitz in its donor times (weights in
+  [0, 1] summing to 1), so forward errors of e can reorder candidates closer
+  than 2 e, and FP32 may legitimately pick either of them;
 * flip set: nodes whose canonical stencils differ; every flip must be a
   near-tie (a mismatch outside the near-ties fails), flips are excluded from
   the gradient comparison and their fraction is bounded per workload.
@@ -88,21 +91,38 @@ def canonical_stencil(ids, w1, with_weight=False):
 def describe_mismatch(mask, gpu_id, gpu_w1, gpu_T, orc_rec, orc_T, limit=6):
     """Text dump of the first nodes of `mask` (for assertion messages)."""
     tmax = orc_T[np.isfinite(orc_T)].max()
+    le = local_error(gpu_T, orc_T)
     rows = []
     for i, j in np.argwhere(mask)[:limit]:
         rows.append(f"({i},{j}) gpu id {int(gpu_id[i, j]):#x} w1 {float(gpu_w1[i, j]):.5f} T {float(gpu_T[i, j]):.7g}"
                     f" | oracle id {int(orc_rec['id'][i, j]):#x} w1 {float(orc_rec['w1'][i, j]):.5f}"
-                    f" T {float(orc_T[i, j]):.7g} margin/maxT {float(orc_rec['margin'][i, j]) / tmax:.2e}")
+                    f" T {float(orc_T[i, j]):.7g} margin/maxT {float(orc_rec['margin'][i, j]) / tmax:.2e}"
+                    f" local err/maxT {float(le[i, j]) / tmax:.2e}")
     return "\n".join(rows)
 
 
-def stencil_compare(gpu_id, gpu_w1, orc_rec, tmax):
+def local_error(T_gpu, T_orc):
+    """max |T_gpu - T_oracle| over each node's 3 x 3 neighbourhood (0 where
+    both are +inf)."""
+    with np.errstate(invalid="ignore"):
+        e = np.abs(np.asarray(T_gpu, np.float64) - np.asarray(T_orc, np.float64))
+    e = np.where(np.isfinite(e), e, 0.0)
+    p = np.pad(e, 1)
+    ny, nx = e.shape
+    return np.max([p[1 + di:1 + di + ny, 1 + dj:1 + dj + nx] for di in (-1, 0, 1) for dj in (-1, 0, 1)], axis=0)
+
+
+def stencil_compare(gpu_id, gpu_w1, orc_rec, tmax, T_gpu=None, T_orc=None):
     """(flips, hard): flips = canonical stencils differ; hard = flips that
-    are not near-ties of the oracle (must be empty)."""
+    are not near-ties of the oracle (must be empty).  With both T given, the
+    near-tie margin includes twice the local forward error."""
     a = canonical_stencil(gpu_id, gpu_w1)
     b = canonical_stencil(orc_rec["id"], orc_rec["w1"])
     flips = a != b
-    hard = flips & (orc_rec["margin"] >= FLIP_MARGIN * tmax)
+    bound = FLIP_MARGIN * tmax
+    if T_gpu is not None and T_orc is not None:
+        bound = bound + 2.0 * local_error(T_gpu, T_orc)
+    hard = flips & (orc_rec["margin"] >= bound)
     return flips, hard
 
 

@@ -73,7 +73,7 @@ def test_batch_matches_oracle(solved):
         assert np.abs(Tb - orc["T"]).max() <= FWD_TOL * tmax, k
         ids = bs.grid(k, "id").cpu().numpy()
         w1 = bs.grid(k, "w1").cpu().numpy()
-        flips, hard = stencil_compare(ids, w1, orc["rec"], tmax)
+        flips, hard = stencil_compare(ids, w1, orc["rec"], tmax, Tb, orc["T"])
         assert int(hard.sum()) == 0, k
         assert rel_l2(bs.grid(k, "graw").cpu().numpy(), orc["graw"], ~flips) < GRAD_TOL, k
 
@@ -153,7 +153,7 @@ def test_batch_config3_sizes_match_oracle():
         assert np.abs(Tb[fin] - To[fin]).max() <= FWD_TOL * tmax, (k, g["src"].shape)
         ids = bs.grid(k, "id").cpu().numpy()
         w1 = bs.grid(k, "w1").cpu().numpy()
-        flips, hard = stencil_compare(ids, w1, orc["rec"], tmax)
+        flips, hard = stencil_compare(ids, w1, orc["rec"], tmax, Tb, To)
         print(f"grid {k} {g['src'].shape} sources {g['nsrc']}: flips {flips.mean():.5f}, hard {int(hard.sum())}")
         assert int(hard.sum()) == 0, (k, g["src"].shape, describe_mismatch(hard, ids, w1, Tb, orc["rec"], To))
         assert flips.mean() <= 0.01, (k, flips.mean())
