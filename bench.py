@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--window", type=float, default=0.0, help="tile queue window (0: kernel default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched workload in the default run")
     p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256", "appb2048"],
                    help="inverse2048: one 2048^2 grid per step (the headline); batch256: 256 grids of sides "
                         "64..1024 per step through rf_batch_solve, with the plain per-grid form beside it")
@@ -398,6 +399,10 @@ def run_ours(args):
                        "gcell_updates_per_s": cell_updates / (phase_ms[1] / 1e3) / 1e9,
                        "phase_ms": dict(zip(names, [round(float(x), 4) for x in phase_ms])),
                        "algo": args.algo}}
+    if world == 1 and not args.no_batch:
+        # the batched workload (256 grids, sides 64..1024) beside the headline:
+        # one graph replay per step against the plain per-grid form
+        line["batch256"] = batch_measure(batch_grids(args.grids), max(3, args.steps // 2), 2, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_solve, iters = oracle_once(n)
         line["cpu_baseline"] = {"value": 1.0 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -426,57 +431,46 @@ def batch_grids(count, seed=0):
     return grids
 
 
-def run_batch(args):
+def batch_measure(grids, steps, warmup, dev, world=1, sampler=None, variant=0):
+    """Time the batched workload through one CUDA-graph replay of
+    BatchSolver (rf_project, rf_batch_solve, rf_project_backward) and, beside
+    it, the plain form: the same grids one by one through the single-grid
+    entry points.  Returns the result dict (rates for this rank's grids)."""
     import torch
 
     from paper_2603_00035_gb300 import api
-    from paper_2603_00035_gb300 import build as B
     from paper_2603_00035_gb300 import replicas
 
-    rank, world, local = dist_info()
-    if world > 1:
-        torch.distributed.init_process_group("nccl")
-    B.build()
-    torch.cuda.set_device(local)
-    all_grids = batch_grids(args.grids)
-    # independent grids shard with no data exchange: each rank solves its own
-    # size-balanced subset
-    grids = [all_grids[i] for i in replicas.shard([g["src"].size for g in all_grids], rank, world)]
-    nodes = sum(g["src"].size for g in all_grids)
-    bs = api.BatchSolver(grids)
+    bs = api.BatchSolver(grids, opts=api.make_opts(variant=variant))
     bs.run()
     torch.cuda.synchronize()
     bs.capture()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         bs.run()
     torch.cuda.synchronize()
-    st = api.Context.get(local).stats()
+    st = api.Context.get(dev).stats()
     if st["status"] != 0 or int(bs.gstat[:, 0].abs().sum()) != 0:
         raise RuntimeError(f"batch status {st}, per-grid {bs.gstat[:, 0].tolist()}")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(local)
-    sampler.start()
-    sampler.wait_first()
+    if sampler:
+        sampler.start()
+        sampler.wait_first()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         bs.run()
     e1.record()
     torch.cuda.synchronize()
-    sampler.stop()
-    rate, total = replicas.job_rate(len(grids) * args.steps, e0.elapsed_time(e1), torch.device("cuda", local))
-    ms = total / args.steps
+    if sampler:
+        sampler.stop()
+    rate, total = replicas.job_rate(len(grids) * steps, e0.elapsed_time(e1), dev)
     sweeps = bs.gstat[:, 1].double().mean().item()
-    # the plain form: one grid after another through the single-grid entry points
-    dev = torch.device("cuda", local)
     per = []
     for g in grids:
-        raw = torch.from_numpy(g["raw"]).to(dev)
-        src = torch.from_numpy(g["src"]).to(dev)
-        gg = torch.from_numpy(g["g"]).to(dev)
-        per.append((raw, src, gg, g["h"]))
+        per.append((torch.from_numpy(g["raw"]).to(dev), torch.from_numpy(g["src"]).to(dev),
+                    torch.from_numpy(g["g"]).to(dev), g["h"]))
 
     def plain():
         for raw, src, gg, h in per:
@@ -487,23 +481,52 @@ def run_batch(args):
 
     plain()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     e0.record()
     plain()
     e1.record()
     torch.cuda.synchronize()
     plain_rate, plain_ms = replicas.job_rate(len(grids), e0.elapsed_time(e1), dev)
-    line = {"metric": f"forward+adjoint solves/s, batch of {len(grids)} grids (sides 64..1024)",
-            "value": rate, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched forward+adjoint, {len(grids)} grids, long side U{{64..1024}}, "
-                                   "half square / half 2:1, 1-8 sources, one persistent launch in a CUDA graph",
-                       "nodes": int(nodes), "mean_sweeps": sweeps,
-                       "l2": "working set > L2 (%.0f MB of fields)" % (nodes * 20 / 1e6)},
+    nodes = sum(g["src"].size for g in grids)
+    return {"value": rate, "unit": UNIT, "ms_per_batch": total / steps, "grids": len(grids), "nodes": int(nodes),
+            "mean_forward_sweep_equivalents": sweeps, "steps": steps, "warmup": warmup,
+            "how": "one CUDA-graph replay of rf_project + rf_batch_solve (tile queue over all grids, record, "
+                   "ordered adjoint over the packed nodes) + rf_project_backward",
             "plain_form": {"value": plain_rate, "unit": UNIT, "ms_per_batch": plain_ms,
                            "how": "rf_project, rf_sweep_forward, rf_adjoint(ordered), rf_project_backward per grid"},
-            "gpu_launches": 3 * args.steps,
+            "speedup_vs_plain": rate / plain_rate}
+
+
+def run_batch(args):
+    import torch
+
+    from paper_2603_00035_gb300 import build as B
+    from paper_2603_00035_gb300 import replicas
+
+    rank, world, local = dist_info()
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    all_grids = batch_grids(args.grids)
+    # independent grids shard with no data exchange: each rank solves its own
+    # size-balanced subset
+    grids = [all_grids[i] for i in replicas.shard([g["src"].size for g in all_grids], rank, world)]
+    nodes = sum(g["src"].size for g in all_grids)
+    sampler = ClockSampler(local)
+    res = batch_measure(grids, args.steps, args.warmup, dev, world, sampler, args.variant)
+    line = {"metric": f"forward+adjoint solves/s, batch of {len(all_grids)} grids (sides 64..1024)",
+            "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched forward+adjoint, {len(all_grids)} grids, long side U{{64..1024}}, "
+                                   "half square / half 2:1, 1-8 sources, CUDA-graph replay",
+                       "nodes": int(nodes), "mean_sweeps": res["mean_forward_sweep_equivalents"],
+                       "l2": "working set > L2 (%.0f MB of fields)" % (nodes * 20 / 1e6)},
+            "plain_form": res["plain_form"],
+            # per replay: project, init, plan, tile map, reset, seed, finish-seed, solve, stats, record,
+            # adjoint-status column, sort keys, gather, unreached, project backward (CUB's sort not counted)
+            "gpu_launches": 15 * args.steps,
             "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -346,23 +346,30 @@ rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src,
                      float *dLdproj5, float *lambda, int algo, void *stream);
 
 /* ---- a10: batched solve ---------------------------------------------------
- * Many grids of uneven size and source count, forward (+ record, + adjoint
- * and parameter gradients when dLdT != NULL) in ONE persistent launch.
+ * Many grids of uneven size and source count, forward + record (+ adjoint
+ * and parameter gradients when dLdT != NULL) in one call.
  * Paper: batched solves across problem instances (Sec. 3.4 "Computational
  * Efficiency"); each grid is the discrete system of rf_sweep_forward and
  * rf_adjoint.
  * Packed layout: every per-node array holds all grids back to back; grid g
  * occupies nodes [descs[g].offset, descs[g].offset + ny*nx) of each plane
  * (row-major inside the grid), and 5-plane arrays have plane stride
- * total_nodes.  descs: DEVICE array of n_grids descriptors; grids are taken
- * in array order by the CTAs, so put the largest first.  max_line >= every
- * grid's max(ny, nx), <= 1024 (sizes the shared memory).  T, rec: outputs
- * (rec required; the adjoint reads it).  dLdT (nullable) and dLdproj5:
- * packed like T and proj5.  grid_status (DEVICE, nullable): 3 int32 per grid
- * = status, forward sweeps, adjoint sweeps.  The call allocates only on
- * first use (lambda workspace); after one call of the same total size it is
- * safe to capture in a CUDA graph.  Device errors also go to the context's
- * status word. */
+ * total_nodes; the offsets increase in descriptor order and the grids do
+ * not overlap (checked on the device: RF_ERR_INVALID_ARG in the status
+ * word).  descs: DEVICE array of n_grids descriptors; put the largest grid
+ * first.  max_line >= every grid's max(ny, nx).  T, rec: outputs (rec
+ * required; the adjoint reads it).  dLdT (nullable) and dLdproj5: packed
+ * like T and proj5.  grid_status (DEVICE, nullable): 3 int32 per grid =
+ * status, forward sweeps (TILES: node updates / nodes, rounded up), adjoint
+ * sweeps (0 for the ordered adjoint).
+ * opts->variant AUTO or TILES: every grid's tiles share one tile queue (see
+ * RF_SWEEP_TILES; band = tile side), then one record pass and the ordered
+ * adjoint over all packed nodes -- a few launches on `stream`.  Line-sweep
+ * variants: one persistent launch, CTAs taking whole grids in array order,
+ * the transposed-sweep adjoint; max_line <= 1024 (shared-memory lines).
+ * Both allocate only on first use (workspace grown to the call's size);
+ * after one call of the same sizes the call is safe to capture in a CUDA
+ * graph.  Device errors also go to the context's status word. */
 typedef struct rf_batch_desc {
   int32_t ny, nx; /* grid shape */
   float h;        /* spacing */

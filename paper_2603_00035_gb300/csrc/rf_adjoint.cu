@@ -17,8 +17,10 @@
 
 #include <cub/device/device_radix_sort.cuh>
 
+#include "rf_adjoint.h"
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
+#include "rf_sweep_tiles.h"
 
 namespace rf {
 
@@ -260,7 +262,10 @@ __global__ void ordered_keys_kernel(const float *T, unsigned *keys, unsigned *va
 }
 
 struct OrderedArgs {
-  int ny, nx;
+  int ny, nx;             // one grid (n_grids == 1)
+  long long n;            // nodes of all grids (plane stride of dT and grad)
+  int n_grids;            // > 1: packed grids, geometry in grids[] (node offsets increasing)
+  const TGrid *grids;
   const uint8_t *src;
   const float *T;
   const uint8_t *id;
@@ -293,9 +298,20 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Grid of packed node p: the last grid whose first node is <= p.
+__device__ __forceinline__ int grid_of(const TGrid *grids, int n_grids, long long p) {
+  int lo = 0, hi = n_grids - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&grids[mid].node_off) <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
   const int lane = threadIdx.x & 31;
-  const long long n = (long long)a.ny * a.nx;
+  const long long n = a.n;
   const unsigned long long tag = (unsigned long long)a.epoch << 32;
   while (true) {
     unsigned base = 0;
@@ -310,11 +326,19 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
     float gsum = 0.0f;
     float dTp[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // partials, loaded before the wait
     bool act = false;
-    int pi = 0, pj = 0;
+    int pi = 0, pj = 0, gny = a.ny, gnx = a.nx;
+    long long goff = 0;
     if (!done) {
       p = a.order[pos];
-      pi = (int)(p / a.nx);
-      pj = (int)(p - (long long)pi * a.nx);
+      if (a.n_grids > 1) {
+        const int g = grid_of(a.grids, a.n_grids, p);
+        goff = __ldg(&a.grids[g].node_off);
+        gny = __ldg(&a.grids[g].ny);
+        gnx = __ldg(&a.grids[g].nx);
+      }
+      const long long lp = p - goff;
+      pi = gnx > 0 ? (int)(lp / gnx) : 0;  // gnx = 0: the grids of an invalid batch were emptied
+      pj = (int)(lp - (long long)pi * gnx);
       const float tp = a.T[p];
       if (!(tp < kInf)) {
         // unreached: no residual, no children
@@ -331,8 +355,8 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
     for (int nb = 0; nb < 8; ++nb) {
       cw[nb] = 0.0f;
       const int ii = pi + nb_dy(nb), jj = pj + nb_dx(nb);
-      if (!done && ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx) {
-        const long long qn = (long long)ii * a.nx + jj;
+      if (!done && ii >= 0 && ii < gny && jj >= 0 && jj < gnx) {
+        const long long qn = goff + (long long)ii * gnx + jj;
         cw[nb] = child_weight(a.id[qn], a.w1[qn], (nb + 4) & 7);
         if (cw[nb] != 0.0f) cmask |= 1u << nb;
       }
@@ -346,7 +370,7 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
 #pragma unroll
         for (int nb = 0; nb < 8; ++nb) {
           if (cmask & (1u << nb)) {
-            const long long qn = (long long)(pi + nb_dy(nb)) * a.nx + (pj + nb_dx(nb));
+            const long long qn = goff + (long long)(pi + nb_dy(nb)) * gnx + (pj + nb_dx(nb));
             const unsigned long long v = ld_relaxed_u64(&a.state[qn]);
             ready = ready && ((v & 0xffffffff00000000ull) == tag);
             acc = fmaf(cw[nb], __uint_as_float((unsigned)v), acc);
@@ -390,11 +414,17 @@ namespace {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-rf_status adjoint_ordered(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, const float *T,
-                          const rf_record *rec, const float *dLdT, float *dLdproj5, float *lambda,
-                          cudaStream_t s) {
+}  // namespace
+
+namespace rf {
+
+// The ordered adjoint of one grid (grids == NULL: shape ny x nx) or of
+// packed grids (grids: device descriptors with increasing node offsets, n
+// nodes in all).
+rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid *grids, int n_grids,
+                          const uint8_t *src, const float *T, const rf_record *rec, const float *dLdT,
+                          float *dLdproj5, float *lambda, cudaStream_t s) {
   ctx->last_stream = s;
-  const long long n = (long long)grid->ny * grid->nx;
   // scratch: keys in/out, values in/out, ticket, abort flag, CUB temp
   size_t temp_bytes = 0;
   if (cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (unsigned *)nullptr, (unsigned *)nullptr,
@@ -426,8 +456,11 @@ rf_status adjoint_ordered(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, 
     return RF_ERR_CUDA;
 
   OrderedArgs a;
-  a.ny = grid->ny;
-  a.nx = grid->nx;
+  a.ny = ny;
+  a.nx = nx;
+  a.n = n;
+  a.n_grids = grids ? n_grids : 1;
+  a.grids = grids;
   a.src = src;
   a.T = T;
   a.id = rec->id;
@@ -461,7 +494,7 @@ rf_status adjoint_ordered(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, 
   return cuda_status(cudaGetLastError());
 }
 
-}  // namespace
+}  // namespace rf
 
 extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, const float *T,
                                 const rf_record *rec, const float *dLdT, float *dLdproj5, float *lambda,
@@ -471,7 +504,9 @@ extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t 
     return RF_ERR_INVALID_ARG;
   if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED) return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
-  if (algo == RF_ADJ_ORDERED) return adjoint_ordered(ctx, grid, src, T, rec, dLdT, dLdproj5, lambda, (cudaStream_t)stream);
+  if (algo == RF_ADJ_ORDERED)
+    return rf::adjoint_ordered(ctx, grid->ny, grid->nx, (long long)grid->ny * grid->nx, nullptr, 1, src, T, rec,
+                               dLdT, dLdproj5, lambda, (cudaStream_t)stream);
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
   const int ny = grid->ny, nx = grid->nx;

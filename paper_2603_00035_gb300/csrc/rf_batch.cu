@@ -1,5 +1,12 @@
 // rf_batch.cu -- a10: many grids of uneven size and source count solved
-// forward + record + adjoint in one persistent launch.
+// forward + record + adjoint.
+//
+// Two paths.  The default (variant AUTO or TILES) puts every grid's tiles in
+// one tile queue (rf_sweep_tiles.cu), so a large grid spreads over all SMs
+// while small ones finish in a few rounds, then records the stencils of all
+// grids in one pass and runs the ordered adjoint over the packed nodes (one
+// radix sort by decreasing T for all grids; a node's children are in its own
+// grid).  The line-sweep variants use the single persistent launch below.
 //
 // Paper: the batched solves of Sec. 3.4 ("batched approach proves
 // essential"), with the same discrete system as rf_sweep_forward / rf_adjoint
@@ -18,8 +25,10 @@
 // parameter gradients.
 #include <algorithm>
 
+#include "rf_adjoint.h"
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
+#include "rf_sweep_tiles.h"
 
 namespace rf {
 
@@ -346,9 +355,100 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchArgs a) {
   }
 }
 
+// a5 for packed grids (blockIdx.y = grid): stencil ids, donor weights and
+// partials of every node at the converged T, and the max residual.
+__global__ void __launch_bounds__(256) batch_record_kernel(const TGrid *grids, long long total, const float *f,
+                                                           float eps, const uint8_t *src, const float *T,
+                                                           uint8_t *id, float *w1, float *dT, DevState *st) {
+  const TGrid g = grids[blockIdx.y];
+  const long long n = (long long)g.ny * g.nx;
+  float local_max = 0.0f;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / g.nx), j = (int)(q - (long long)i * g.nx);
+    const long long p = g.node_off + q;
+    uint8_t idv;
+    float w1v, d[5], r;
+    record_node(f + g.node_off, total, q, i, j, g.ny, g.nx, g.h, eps, src[p] != 0, T + g.node_off, true, idv,
+                w1v, d, r);
+    id[p] = idv;
+    w1[p] = w1v;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) dT[c * total + p] = d[c];
+    local_max = fmaxf(local_max, fabsf(r));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&st->max_res_bits, __float_as_uint(local_max));
+}
+
+// Adjoint column of the per-grid status (the ordered adjoint has no sweeps).
+__global__ void batch_adj_status_kernel(int *gstat, int n_grids) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_grids; g += gridDim.x * blockDim.x)
+    gstat[3 * g + 2] = 0;
+}
+
 }  // namespace rf
 
 using namespace rf;
+
+namespace {
+
+// The tile-queue path of rf_batch_solve (see the file comment).
+rf_status batch_tiles(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids, int64_t total_nodes, int32_t max_line,
+                      const float *proj5, float eps, const uint8_t *src, const rf_opts &o, float *T,
+                      rf_record *rec, const float *dLdT, float *dLdproj5, int32_t *grid_status, cudaStream_t s) {
+  const int ts = rf::tile_side(o.variant == RF_SWEEP_TILES ? o.band : 0);
+  const int ncap = rf::tiles_cap(n_grids, total_nodes, max_line, ts);
+  rf_status rs;
+  if ((rs = ensure(&ctx->tilebuf, &ctx->tilebuf_cap, rf::tile_work_bytes(n_grids, ncap, ts))) != RF_OK) return rs;
+  if ((rs = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)total_nodes)) != RF_OK) return rs;
+  if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2)) != RF_OK) return rs;
+  cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
+  cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
+  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 4, s);
+  cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
+  int *has_src = ctx->changed + o.max_sweeps;  // per-grid sources are checked by the seed kernel
+  rf::init_state(T, src, total_nodes, o.mode == RF_MODE_WARM, ctx->state, has_src, ctx->num_sms, s);
+  LaunchCtl ctl;
+  ctl.st = ctx->state;
+  ctl.abort = ctx->changed + o.max_sweeps + 1;
+  ctl.timeout_ns = ctx->timeout_ns;
+  const rf::TileWork w = rf::tile_work_carve(ctx->tilebuf, n_grids, ncap, ts);
+  rf::TileLaunch L;
+  L.num_sms = ctx->num_sms;
+  L.ts = ts;
+  L.n_grids = n_grids;
+  L.descs = descs;
+  L.ny = L.nx = 0;
+  L.h = 0.0f;
+  L.max_line = max_line;
+  L.total_nodes = total_nodes;
+  L.ntiles_cap = ncap;
+  L.eps = eps;
+  L.proj5 = proj5;
+  L.src = src;
+  L.T = T;
+  L.Tb = ctx->tbuf;
+  L.warm = o.mode == RF_MODE_WARM;
+  L.max_sweeps = o.max_sweeps;
+  L.tol = o.tol;
+  L.rtol = o.rtol;
+  L.window = o.window;
+  L.grid_status = grid_status;
+  if ((rs = rf::tiles_launch(L, w, ctl, s)) != RF_OK) return rs;
+  cudaMemsetAsync(&ctx->state->max_res_bits, 0, sizeof(unsigned), s);
+  const long long per_grid = std::max<long long>(1, total_nodes / n_grids);
+  const int gx = std::max(1, std::min(blocks_for(per_grid, 256, ctx->num_sms * 8), 65535));
+  batch_record_kernel<<<dim3(gx, n_grids), 256, 0, s>>>(w.grids, total_nodes, proj5, eps, src, T, rec->id, rec->w1,
+                                                        rec->dT, ctx->state);
+  if ((rs = cuda_status(cudaGetLastError())) != RF_OK) return rs;
+  if (grid_status) batch_adj_status_kernel<<<blocks_for(n_grids, 256, 64), 256, 0, s>>>(grid_status, n_grids);
+  if (!dLdT) return cuda_status(cudaGetLastError());
+  return rf::adjoint_ordered(ctx, 0, 0, total_nodes, w.grids, n_grids, src, T, rec, dLdT, dLdproj5, nullptr, s);
+}
+
+}  // namespace
 
 extern "C" rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids, int64_t total_nodes,
                                     int32_t max_line, const float *proj5, float eps, const uint8_t *src,
@@ -357,15 +457,24 @@ extern "C" rf_status rf_batch_solve(rf_ctx *ctx, const rf_batch_desc *descs, int
   if (!ctx || !descs || n_grids < 1 || total_nodes < 1 || !proj5 || !src || !T || !rec || !rec->id || !rec->w1 ||
       !rec->dT)
     return RF_ERR_INVALID_ARG;
-  if (max_line < 1 || max_line > kBThreads * kBCells || !(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
+  if (max_line < 1 || !(eps >= 0.0f)) return RF_ERR_INVALID_ARG;
   if (dLdT && !dLdproj5) return RF_ERR_INVALID_ARG;
-  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0};
+  rf_opts o = {0.0f, 64, RF_MODE_COLD, 0, 0, 1e-6f, 0, 0.0f};
   if (opts) o = *opts;
-  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM))
+  if (o.max_sweeps < 1 || !(o.tol >= 0.0f) || !(o.rtol >= 0.0f) || (o.mode != RF_MODE_COLD && o.mode != RF_MODE_WARM) ||
+      !(o.window >= 0.0f))
     return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
+  if (o.variant == RF_SWEEP_AUTO || o.variant == RF_SWEEP_TILES) {
+    // launch-grid limits of the per-grid kernels and the 32-bit sort
+    if (n_grids > 65535 || total_nodes >= (1LL << 31)) return RF_ERR_INVALID_ARG;
+    return batch_tiles(ctx, descs, n_grids, total_nodes, max_line, proj5, eps, src, o, T, rec, dLdT, dLdproj5,
+                       grid_status, s);
+  }
+  // the persistent kernel keeps whole lines of a grid in shared memory
+  if (max_line > kBThreads * kBCells) return RF_ERR_INVALID_ARG;
   rf_status rs;
   if (dLdT && (rs = ensure(&ctx->lbuf, &ctx->lbuf_cap, (size_t)total_nodes)) != RF_OK) return rs;
   if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)2)) != RF_OK) return rs;

@@ -410,6 +410,11 @@ __global__ void check_source_kernel(const int *has_src, DevState *st) {
   if (threadIdx.x == 0 && *has_src == 0) set_error(st, RF_ERR_NO_SOURCE);
 }
 
+void init_state(float *T, const uint8_t *src, long long n, int warm, DevState *st, int *has_src, int num_sms,
+                cudaStream_t s) {
+  init_kernel<<<blocks_for(n, 256, num_sms * 8), 256, 0, s>>>(T, src, n, warm, st, has_src);
+}
+
 struct RecordArgs {
   int ny, nx;
   float h, eps;
@@ -540,7 +545,8 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   // tile queue: the default when its workspace can be allocated
   if (o.variant == RF_SWEEP_TILES || o.variant == RF_SWEEP_AUTO) {
     const int ts = rf::tile_side(o.variant == RF_SWEEP_TILES ? o.band : 0);
-    rf_status rt = ensure(&ctx->tilebuf, &ctx->tilebuf_cap, rf::tile_work_bytes(ny, nx, ts));
+    const int ncap = rf::tiles_cap(1, n, std::max(ny, nx), ts);
+    rf_status rt = ensure(&ctx->tilebuf, &ctx->tilebuf_cap, rf::tile_work_bytes(1, ncap, ts));
     if (rt == RF_OK) rt = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)n);
     if (rt == RF_OK) rt = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2);
     if (rt != RF_OK && o.variant == RF_SWEEP_TILES) return rt;
@@ -557,9 +563,30 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
       ctl.st = ctx->state;
       ctl.abort = ctx->changed + o.max_sweeps + 1;
       ctl.timeout_ns = ctx->timeout_ns;
-      const rf::TileWork w = rf::tile_work_carve(ctx->tilebuf, ny, nx, ts);
-      rt = rf::tiles_launch(ctx->num_sms, ny, nx, ts, grid->h, eps, proj5, src, T, ctx->tbuf,
-                            o.mode == RF_MODE_WARM, o.max_sweeps, o.tol, o.rtol, o.window, w, ctl, s);
+      const rf::TileWork w = rf::tile_work_carve(ctx->tilebuf, 1, ncap, ts);
+      rf::TileLaunch L;
+      L.num_sms = ctx->num_sms;
+      L.ts = ts;
+      L.n_grids = 1;
+      L.descs = nullptr;
+      L.ny = ny;
+      L.nx = nx;
+      L.h = grid->h;
+      L.max_line = std::max(ny, nx);
+      L.total_nodes = n;
+      L.ntiles_cap = ncap;
+      L.eps = eps;
+      L.proj5 = proj5;
+      L.src = src;
+      L.T = T;
+      L.Tb = ctx->tbuf;
+      L.warm = o.mode == RF_MODE_WARM;
+      L.max_sweeps = o.max_sweeps;
+      L.tol = o.tol;
+      L.rtol = o.rtol;
+      L.window = o.window;
+      L.grid_status = nullptr;
+      rt = rf::tiles_launch(L, w, ctl, s);
       if (rt != RF_OK) return rt;
       if (rec) {
         RecordArgs r;

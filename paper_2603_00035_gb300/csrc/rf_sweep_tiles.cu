@@ -38,6 +38,13 @@
 //
 // The dependent chain is the number of Jacobi iterations along the path of
 // the front (a few thousand at 2048^2) instead of sweeps x grid lines.
+//
+// The same kernel solves a batch of grids (rf_batch_solve, Sec. 3.4's
+// batched solves): the grids' tiles share one queue, each tile knows its
+// grid (per-grid descriptor: shape, spacing, offsets into the packed
+// arrays), and keys are normalised per grid to tile crossings (T divided by
+// tile side x mean edge cost), so a window means the same front advance on
+// every grid whatever its size.  A single grid is a batch of one.
 #include <algorithm>
 
 #include "rf_cone.cuh"
@@ -58,11 +65,11 @@ struct TileSlot {
   unsigned kmin;   // float bits of the smallest queued key
   unsigned pad;
 };
-// ctrl layout (unsigned words): 3 slots x 4, mean edge cost, its sum, tiles
-// that published a new version [3] (by round mod 3)
-constexpr int kCtrlEbar = kSlots * 4;
-constexpr int kCtrlEsum = kCtrlEbar + 1;
-constexpr int kCtrlMoved = kCtrlEbar + 2;
+// ctrl layout (unsigned words): 3 slots x 4, the tile count, a spare word,
+// tiles that published a new version [3] (by round mod 3)
+constexpr int kCtrlNT = kSlots * 4;      // tiles of all grids (plan kernel)
+constexpr int kCtrlMoved = kCtrlNT + 2;  // [3]
+
 
 template <int TS>
 struct TileGeom {
@@ -85,13 +92,17 @@ struct alignas(16) GroupSmem {
   unsigned long long rowm[2][TileGeom<TS>::TW];            // change masks (see colspace)
   unsigned nkey[9];                                        // smallest changed boundary time per neighbour
   int par[9];                                              // round-start buffer of the 3 x 3 tiles
-  int tile, go, first;
+  float t0[TileGeom<TS>::NODES];  // node values at the start of the visit
+  TGrid gd;      // grid of the current tile
+  int tile, go, first, gid;
   unsigned key;
+  unsigned upd;  // node updates of the current visit
 };
 
 struct TileArgs {
-  int ny, nx, ts, tny, tnx, ntiles;
-  float h, eps;
+  int n_grids, ts, ntiles_cap;  // tiles of all grids <= ntiles_cap (strides of the queue arrays)
+  long long plane;              // nodes of all grids: plane stride of the 5-plane fields
+  float eps;
   const float *f;
   const uint8_t *src;
   float *T[2];  // buffer 0 = the caller's T, buffer 1 = workspace
@@ -181,15 +192,14 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
   const int sr = row + 1, sc = col + 1;
 
   const TileWork &w = a.w;
-  const int NT = a.ntiles;
-  const long long plane = (long long)a.ny * a.nx;
+  const int NT = (int)w.ctrl[kCtrlNT];  // tiles of all grids
+  const int NC = a.ntiles_cap;          // stride of the per-round queue arrays
+  const long long plane = a.plane;
   TileSlot *slots = reinterpret_cast<TileSlot *>(w.ctrl);
   unsigned *moved_ct = w.ctrl + kCtrlMoved;
-  unsigned long long my_updates = 0, my_warp_evals = 0;
+  unsigned long long my_warp_evals = 0;
   bool converged = false, abort = false, prev_cert = false;
   int r = 1;
-  const float ebar = __uint_as_float(w.ctrl[kCtrlEbar]);  // mean edge cost (seed kernel)
-  const float delta = a.window * (float)TS * ebar;
 
   for (;; ++r) {
     TileSlot *cur = slots + (r % kSlots);
@@ -215,21 +225,28 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
     }
     prev_cert = cert;
     if (r > a.max_rounds) break;
-    const float theta = cert ? kInf : __uint_as_float(__ldcg(&cur->kmin)) + delta;
+    const float theta = cert ? kInf : __uint_as_float(__ldcg(&cur->kmin)) + a.window;
 
     while (true) {
       if (gt == 0) {
         const unsigned k = atomicAdd(&cur->grab, 1u);
         S.go = k < n;
+        int t = -1;
         if (k < n && cert) {
-          S.tile = (int)k;
+          t = (int)k;
           S.key = 0u;
         } else if (k < n) {
-          const int t = __ldcg(&w.list[(size_t)(r % kSlots) * NT + k]);
-          S.tile = t;
-          unsigned *kp = &w.key[(size_t)(r & 1) * NT + t];
+          t = __ldcg(&w.list[(size_t)(r % kSlots) * NC + k]);
+          unsigned *kp = &w.key[(size_t)(r & 1) * NC + t];
           S.key = __ldcg(kp);
           __stcg(kp, kInfBits);
+        }
+        if (t >= 0) {
+          // the tile's grid, kept in shared memory for the visit
+          const int gid = a.n_grids == 1 ? 0 : __ldg(&w.tile_grid[t]);
+          S.tile = t;
+          S.gid = gid;
+          S.gd = w.grids[gid];
         }
       }
       group_sync<NG>(bar);
@@ -238,18 +255,23 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
       const unsigned kb = S.key;
       if (__uint_as_float(kb) > theta) {
         // too far ahead of the front: keep it for a later round
-        if (gt == 0) push(w, NT, t, r + 1, kb);
+        if (gt == 0) push(w, NC, t, r + 1, kb);
         group_sync<NG>(bar);
         continue;
       }
-      const int ti = t / a.tnx, tj = t - ti * a.tnx;
+      const int gid = S.gid;
+      const TGrid &gd = S.gd;
+      const int tl = t - gd.tile_off;
+      const int ti = tl / gd.tnx, tj = tl - ti * gd.tnx;
       const int i0 = ti * TS, j0 = tj * TS;
+      const int gny = gd.ny, gnx = gd.nx;
+      const long long goff = gd.node_off;
       // Everything that does not depend on the neighbours' buffer parities is
       // requested first, so that a visit pays two dependent global round
       // trips (parities, then T) instead of one per step.
       const int i = i0 + row, j = j0 + col;
-      const bool inb = (i < a.ny) && (j < a.nx);
-      const long long p = (long long)i * a.nx + j;
+      const bool inb = (i < gny) && (j < gnx);
+      const long long p = goff + (long long)i * gnx + j;
       float fl[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       bool is_src = false;
       if (inb) {
@@ -273,8 +295,8 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
         const int di = gt / 3 - 1, dj = gt % 3 - 1;
         const int ni = ti + di, nj = tj + dj;
         int pp = 0;
-        if (ni >= 0 && ni < a.tny && nj >= 0 && nj < a.tnx)
-          pp = start_parity(__ldcg(&w.tstate[ni * a.tnx + nj]), r);
+        if (ni >= 0 && ni < gd.tny && nj >= 0 && nj < gd.tnx)
+          pp = start_parity(__ldcg(&w.tstate[gd.tile_off + ni * gd.tnx + nj]), r);
         S.par[gt] = pp;
         S.nkey[gt] = kInfBits;
       }
@@ -283,10 +305,11 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
         S.rowm[0][gt] = 0ull;
         S.rowm[1][gt] = 0ull;
       }
+      if (gt == 0) S.upd = 0u;
       // this thread's node: cone-form constants into shared memory
       if (inb) {
         float4 q[kPlanes];
-        node_record(fl[0], fl[1], fl[2], fl[3], fl[4], a.h, a.eps, is_src, q);
+        node_record(fl[0], fl[1], fl[2], fl[3], fl[4], gd.h, a.eps, is_src, q);
 #pragma unroll
         for (int c = 0; c < kPlanes; ++c) S.q[c][gt] = q[c];
       }
@@ -298,10 +321,10 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
       // value differs from this tile's previous visit seed the change masks
       if (gt < G::HALO) {
         float v = kInf;
-        if (gi >= 0 && gi < a.ny && gj >= 0 && gj < a.nx) {
+        if (gi >= 0 && gi < gny && gj >= 0 && gj < gnx) {
           const int di = (hr == 0) ? -1 : (hr == G::TW - 1) ? 1 : 0;
           const int dj = (hc == 0) ? -1 : (hc == G::TW - 1) ? 1 : 0;
-          v = __ldcg(a.T[S.par[(di + 1) * 3 + dj + 1]] + (long long)gi * a.nx + gj);
+          v = __ldcg(a.T[S.par[(di + 1) * 3 + dj + 1]] + goff + (long long)gi * gnx + gj);
         }
         S.Ts[0][hr][hc] = v;
         S.Ts[1][hr][hc] = v;
@@ -309,7 +332,7 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
         __stcg(hp, v);
       }
       const bool upd = inb && !is_src;
-      const float tinit = tcur;
+      S.t0[gt] = tcur;
       S.Ts[0][sr][sc] = tcur;
       S.Ts[1][sr][sc] = tcur;
       // first visit: the sources (cold) or every node (warm) start changed;
@@ -339,7 +362,7 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
             tnew = cone_min(S.q[0][gt], S.q[1][gt], S.q[2][gt], S.q[3][gt], S.q[4][gt], S.q[5][gt], Tn);
           }
           if (lane == 0) {
-            my_updates += (unsigned long long)__popc(dball);
+            atomicAdd(&S.upd, (unsigned)__popc(dball));
             my_warp_evals += 1;
           }
         }
@@ -370,11 +393,13 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
       }
 
       // publish: a new version only if some node moved beyond the tolerance
-      const bool moved = upd && node_changed(tcur, tinit, a.tol, a.rtol);
+      const bool moved = upd && node_changed(tcur, S.t0[gt], a.tol, a.rtol);
       if (group_sync_or<NG>(bar, moved)) {
-        if (inb) __stcg(Tout + p, tcur);
+        if (inb) __stcg(Tout + gd.node_off + (long long)(i0 + row) * gd.nx + (j0 + col), tcur);
         if (moved) {
-          const unsigned kbits = __float_as_uint(tcur);
+          // key of the neighbours this node queues: its new time in tile
+          // crossings of this grid
+          const unsigned kbits = __float_as_uint(tcur * gd.inv_scale);
           const bool top = row == 0, bot = row == TS - 1, lft = col == 0, rgt = col == TS - 1;
           if (top) atomicMin(&S.nkey[1], kbits);
           if (bot) atomicMin(&S.nkey[7], kbits);
@@ -392,13 +417,18 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
         }
         if (gt < 9 && gt != 4 && S.nkey[gt] != kInfBits) {
           const int ni = ti + gt / 3 - 1, nj = tj + gt % 3 - 1;
-          if (ni >= 0 && ni < a.tny && nj >= 0 && nj < a.tnx) push(w, NT, ni * a.tnx + nj, r + 1, S.nkey[gt]);
+          if (ni >= 0 && ni < gd.tny && nj >= 0 && nj < gd.tnx)
+            push(w, NC, gd.tile_off + ni * gd.tnx + nj, r + 1, S.nkey[gt]);
         }
       }
       if (gt == 0) {
         __stcg(&w.visits[t], __ldcg(&w.visits[t]) + 1u);
+        if (S.upd) {
+          atomicAdd(&w.gupd[gid], (unsigned long long)S.upd);
+          atomicAdd(&w.counters[0], (unsigned long long)S.upd);
+        }
         // a visit cut short by the iteration cap is resumed next round
-        if (capped) push(w, NT, t, r + 1, kb);
+        if (capped) push(w, NC, t, r + 1, kb);
       }
       group_sync<NG>(bar);
     }
@@ -407,15 +437,20 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
       break;
     }
   }
-  if (lane == 0 && (my_updates || my_warp_evals)) {
-    atomicAdd(&w.counters[0], my_updates);
-    atomicAdd(&w.counters[1], my_warp_evals);
-  }
+  if (lane == 0 && my_warp_evals) atomicAdd(&w.counters[1], my_warp_evals);
   if (!abort) {
-    // hand the latest version of every tile back in the caller's buffer
-    for (long long q = (long long)blockIdx.x * blockDim.x + tid; q < plane; q += (long long)gridDim.x * blockDim.x) {
-      const int qi = (int)(q / a.nx), qj = (int)(q - (long long)qi * a.nx);
-      if (__ldcg(&w.tstate[(qi / TS) * a.tnx + qj / TS]) & 1u) a.T[0][q] = __ldcg(a.T[1] + q);
+    // hand the latest version of every tile back in the caller's buffer: a
+    // tile per group, one thread per node
+    for (int t = blockIdx.x * G::GROUPS + grp; t < NT; t += gridDim.x * G::GROUPS) {
+      if ((__ldcg(&w.tstate[t]) & 1u) == 0u) continue;
+      const int gid = a.n_grids == 1 ? 0 : __ldg(&w.tile_grid[t]);
+      const TGrid gd = w.grids[gid];
+      const int tl = t - gd.tile_off;
+      const int i = (tl / gd.tnx) * TS + row, j = (tl % gd.tnx) * TS + col;
+      if (i < gd.ny && j < gd.nx) {
+        const long long q = gd.node_off + (long long)i * gd.nx + j;
+        a.T[0][q] = __ldcg(a.T[1] + q);
+      }
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
@@ -425,13 +460,105 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
   }
 }
 
-// Workspace reset and the mean edge cost of the field (mean of
-// (|m_x|_M + |m_y|_M) / 2, the time scale of the delta-stepping window).
-__global__ void tile_seed_kernel(TileArgs a, float *esum) {
+// ---- seeding -----------------------------------------------------------------
+// Plan of one grid (the single-grid entry point): its descriptor and the
+// tile count.
+__global__ void tile_plan_single_kernel(TileWork w, int ny, int nx, float h, int ts) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  TGrid g;
+  g.node_off = 0;
+  g.ny = ny;
+  g.nx = nx;
+  g.tny = (ny + ts - 1) / ts;
+  g.tnx = (nx + ts - 1) / ts;
+  g.tile_off = 0;
+  g.h = h;
+  g.inv_scale = 0.0f;
+  g.esum = 0.0f;
+  g.has_src = 0;
+  g.pad = 0;
+  w.grids[0] = g;
+  w.ctrl[kCtrlNT] = (unsigned)(g.tny * g.tnx);
+}
+
+// Plan of a batch: every grid's descriptor with its first tile (an
+// exclusive scan of the tile counts, in descriptor order), and the tile
+// count.  One CTA.  Descriptors that are not a valid packing (empty or
+// non-positive spacing, outside [0, total), out of order or overlapping)
+// raise RF_ERR_INVALID_ARG and leave every grid empty, so that no later
+// kernel of the call touches memory through them.
+__global__ void tile_plan_batch_kernel(TileWork w, const rf_batch_desc *descs, int n_grids, int ts,
+                                       long long total, int max_line, int ntiles_cap, DevState *st) {
+  __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long s_total;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int per = (n_grids + nth - 1) / nth;
+  const int g0 = tid * per, g1 = min(n_grids, g0 + per);
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  unsigned long long mine = 0;
+  int bad = 0;
+  for (int g = g0; g < g1; ++g) {
+    const rf_batch_desc d = descs[g];
+    const long long end = d.offset + (long long)d.ny * d.nx;
+    bad |= d.ny < 1 || d.nx < 1 || d.ny > max_line || d.nx > max_line || !(d.h > 0.0f) || d.offset < 0 ||
+           end > total || (g + 1 < n_grids && descs[g + 1].offset < end);
+    if (!bad) mine += (unsigned long long)((d.ny + ts - 1) / ts) * (unsigned long long)((d.nx + ts - 1) / ts);
+  }
+  if (bad) atomicOr(&s_bad, 1);
+  part[tid] = mine;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long run = 0;
+    for (int k = 0; k < nth; ++k) {
+      const unsigned long long v = part[k];
+      part[k] = run;
+      run += v;
+    }
+    s_total = run;
+    // the workspace holds ntiles_cap tiles, a bound for any valid packing
+    if (run > (unsigned long long)ntiles_cap) s_bad = 1;
+  }
+  __syncthreads();
+  const bool any_bad = s_bad != 0;
+  if (tid == 0) {
+    w.ctrl[kCtrlNT] = any_bad ? 0u : (unsigned)s_total;
+    if (any_bad) set_error(st, RF_ERR_INVALID_ARG);
+  }
+  unsigned long long off = any_bad ? 0ull : part[tid];
+  for (int g = g0; g < g1; ++g) {
+    const rf_batch_desc d = descs[g];
+    TGrid t;
+    t.node_off = any_bad ? 0 : d.offset;
+    t.ny = any_bad ? 0 : d.ny;
+    t.nx = any_bad ? 0 : d.nx;
+    t.tny = (t.ny + ts - 1) / ts;
+    t.tnx = (t.nx + ts - 1) / ts;
+    t.tile_off = (int)off;
+    t.h = any_bad ? 1.0f : d.h;
+    t.inv_scale = 0.0f;
+    t.esum = 0.0f;
+    t.has_src = 0;
+    t.pad = 0;
+    w.grids[g] = t;
+    off += (unsigned long long)t.tny * (unsigned long long)t.tnx;
+  }
+}
+
+// tile -> grid map of a batch (blockIdx.y = grid).
+__global__ void tile_map_kernel(TileWork w) {
+  const TGrid g = w.grids[blockIdx.y];
+  const int n = g.tny * g.tnx;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    w.tile_grid[g.tile_off + k] = (int)blockIdx.y;
+}
+
+// Workspace reset (tiles_cap tiles) and the slots.
+__global__ void tile_reset_kernel(TileArgs a) {
   const TileWork &w = a.w;
-  const int NT = a.ntiles;
+  const int NC = a.ntiles_cap;
   const int halo = 4 * a.ts + 4;
-  const long long plane = (long long)a.ny * a.nx;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g0 == 0) {
@@ -442,71 +569,103 @@ __global__ void tile_seed_kernel(TileArgs a, float *esum) {
       slots[k].kmin = kInfBits;
     }
   }
-  for (long long t = g0; t < NT; t += stride) {
+  for (long long t = g0; t < NC; t += stride) {
     w.tstate[t] = 0u;
     w.visits[t] = 0u;
     w.key[t] = kInfBits;
-    w.key[NT + t] = kInfBits;
+    w.key[NC + t] = kInfBits;
     w.queued[t] = a.warm ? 1u : 0u;
   }
-  for (long long k = g0; k < (long long)NT * halo; k += stride) w.halo[k] = kInf;
-  float part = 0.0f;
-  for (long long p = g0; p < plane; p += stride) {
-    const float l11 = a.f[p], l21 = a.f[plane + p], l22 = a.f[2 * plane + p];
-    const float m11 = fmaf(l11, l11, a.eps), m22 = fmaf(l21, l21, fmaf(l22, l22, a.eps));
-    part += 0.5f * a.h * (sqrtf(m11) + sqrtf(m22));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(esum, part);
+  for (long long k = g0; k < (long long)NC * halo; k += stride) w.halo[k] = kInf;
+  for (long long g = g0; g < a.n_grids; g += stride) w.gupd[g] = 0ull;
 }
 
-// Queue the first round (runs after tile_seed_kernel), key 0: every tile
-// (warm) or every tile that holds a source or one of its neighbours (cold: a
-// source never changes, so the tiles across a tile edge next to it must see
-// it in their halo on their own first visit).
-__global__ void tile_queue_kernel(TileArgs a) {
+// Per grid (blockIdx.y): the sum of the edge costs (|m_x|_M + |m_y|_M) / 2
+// (the time scale of the queue keys), and the first round's queue, key 0:
+// every tile (warm) or every tile that holds a source or one of its
+// neighbours (cold: a source never changes, so the tiles across a tile edge
+// next to it must see it in their halo on their own first visit).
+__global__ void tile_seed_kernel(TileArgs a) {
   const TileWork &w = a.w;
-  const int NT = a.ntiles;
+  const int NC = a.ntiles_cap;
+  TGrid *gp = w.grids + blockIdx.y;
+  const TGrid g = *gp;
+  const long long n = (long long)g.ny * g.nx;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a.warm) {
-    for (long long t = g0; t < NT; t += stride) {
-      w.key[NT + t] = 0u;  // round 1 reads key slot 1
-      w.list[(size_t)(1 % kSlots) * NT + t] = (int)t;
-    }
-    return;
-  }
-  const long long plane = (long long)a.ny * a.nx;
-  for (long long p = g0; p < plane; p += stride) {
+  float part = 0.0f;
+  int any_src = 0;
+  for (long long q = g0; q < n; q += stride) {
+    const long long p = g.node_off + q;
+    const float l11 = a.f[p], l21 = a.f[a.plane + p], l22 = a.f[2 * a.plane + p];
+    const float m11 = fmaf(l11, l11, a.eps), m22 = fmaf(l21, l21, fmaf(l22, l22, a.eps));
+    part += 0.5f * g.h * (sqrtf(m11) + sqrtf(m22));
     if (!a.src[p]) continue;
-    const int i = (int)(p / a.nx), j = (int)(p - (long long)i * a.nx);
+    any_src = 1;
+    if (a.warm) continue;
+    const int i = (int)(q / g.nx), j = (int)(q - (long long)i * g.nx);
     for (int di = -1; di <= 1; ++di)
       for (int dj = -1; dj <= 1; ++dj) {
         const int ii = i + di, jj = j + dj;
-        if (ii < 0 || ii >= a.ny || jj < 0 || jj >= a.nx) continue;
-        const int t = (ii / a.ts) * a.tnx + jj / a.ts;
-        atomicMin(&w.key[NT + t], 0u);
-        enqueue(w, NT, t, 1);
+        if (ii < 0 || ii >= g.ny || jj < 0 || jj >= g.nx) continue;
+        const int t = g.tile_off + (ii / a.ts) * g.tnx + jj / a.ts;
+        atomicMin(&w.key[NC + t], 0u);  // round 1 reads key slot 1
+        enqueue(w, NC, t, 1);
       }
+  }
+  if (a.warm) {
+    const int nt = g.tny * g.tnx;
+    for (long long k = g0; k < nt; k += stride) {
+      const int t = g.tile_off + (int)k;
+      w.key[NC + t] = 0u;
+      w.list[(size_t)(1 % kSlots) * NC + t] = t;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+    any_src |= __shfl_xor_sync(0xffffffffu, any_src, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&gp->esum, part);
+    if (any_src) atomicOr(&gp->has_src, 1);
   }
 }
 
-__global__ void tile_finish_seed_kernel(TileArgs a, const float *esum) {
-  if (threadIdx.x != 0) return;
-  TileSlot *slots = reinterpret_cast<TileSlot *>(a.w.ctrl);
-  if (a.warm) slots[1 % kSlots].count = (unsigned)a.ntiles;
-  slots[1 % kSlots].kmin = 0u;
-  const float ebar = *esum / (float)((long long)a.ny * a.nx);
-  a.w.ctrl[kCtrlEbar] = __float_as_uint(ebar > 0.0f && ebar < kInf ? ebar : 1.0f);
+// Keys of each grid in tile crossings; round 1's queue minimum; sources.
+__global__ void tile_finish_seed_kernel(TileArgs a) {
+  const TileWork &w = a.w;
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < a.n_grids; gi += gridDim.x * blockDim.x) {
+    TGrid &g = w.grids[gi];
+    const float ebar = g.esum / (float)((long long)g.ny * g.nx);
+    g.inv_scale = (ebar > 0.0f && ebar < kInf) ? 1.0f / ((float)a.ts * ebar) : 1.0f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    TileSlot *slots = reinterpret_cast<TileSlot *>(w.ctrl);
+    if (a.warm) slots[1 % kSlots].count = w.ctrl[kCtrlNT];
+    slots[1 % kSlots].kmin = 0u;
+  }
 }
 
-// Statistics of the solve: node updates and their sweep equivalent.
-__global__ void tile_stats_kernel(const unsigned long long *counters, DevState *st, long long n) {
-  if (threadIdx.x != 0) return;
-  const unsigned long long u = counters[0];
-  st->cell_updates = u;
-  st->sweeps = (int)((u + (unsigned long long)n - 1ull) / (unsigned long long)n);
+// Statistics: node updates of the solve, their sweep equivalent, and per
+// grid (batch) status / sweep equivalent.
+__global__ void tile_stats_kernel(TileArgs a, DevState *st, int *grid_status, int converged_only_global) {
+  const TileWork &w = a.w;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long u = w.counters[0];
+    st->cell_updates = u;
+    st->sweeps = (int)((u + (unsigned long long)a.plane - 1ull) / (unsigned long long)a.plane);
+  }
+  if (!grid_status) return;
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < a.n_grids; gi += gridDim.x * blockDim.x) {
+    const TGrid g = w.grids[gi];
+    const unsigned long long n = (unsigned long long)g.ny * (unsigned long long)g.nx;
+    const int code = !g.has_src ? RF_ERR_NO_SOURCE : (st->converged ? RF_OK : RF_ERR_NOT_CONVERGED);
+    grid_status[3 * gi] = code;
+    grid_status[3 * gi + 1] = n ? (int)((w.gupd[gi] + n - 1ull) / n) : 0;
+    if (code != RF_OK) set_error(st, code);
+  }
+  (void)converged_only_global;
 }
 
 }  // namespace rf
@@ -515,33 +674,48 @@ namespace rf {
 
 int tile_side(int requested) { return requested >= 32 ? 32 : 16; }
 
-int tiles_count(int ny, int nx, int ts) { return ((ny + ts - 1) / ts) * ((nx + ts - 1) / ts); }
-
-size_t tile_work_bytes(int ny, int nx, int ts) {
-  const size_t NT = (size_t)tiles_count(ny, nx, ts);
-  // counters, ctrl, then tstate, visits, queued, key[2], list[3], halo
-  return 64 + 256 + NT * 4 * 5 + NT * 4 * kSlots + NT * (size_t)(4 * ts + 4) * 4;
+int tiles_cap(int n_grids, long long total_nodes, int max_line, int ts) {
+  // ceil(a/t) ceil(b/t) <= ab/t^2 + (a + b)/t + 1 per grid; with floors and
+  // a, b <= max_line the sum is below total/t^2 + 1 + grids (2 max_line/t + 2)
+  const long long cap =
+      total_nodes / ((long long)ts * ts) + 1 + (long long)n_grids * (2LL * max_line / ts + 2);
+  return (int)std::min(cap, (long long)1 << 30);
 }
 
-TileWork tile_work_carve(void *base, int ny, int nx, int ts) {
-  const size_t NT = (size_t)tiles_count(ny, nx, ts);
+size_t tile_work_bytes(int n_grids, int ntiles_cap, int ts) {
+  const size_t NC = (size_t)ntiles_cap;
+  // counters, ctrl, grids, per-grid updates, then tstate, visits, queued,
+  // key[2], list[3], tile -> grid, halo
+  return 64 + 256 + (size_t)n_grids * sizeof(TGrid) + (size_t)n_grids * 8 + NC * 4 * 5 + NC * 4 * kSlots +
+         NC * 4 + NC * (size_t)(4 * ts + 4) * 4;
+}
+
+TileWork tile_work_carve(void *base, int n_grids, int ntiles_cap, int ts) {
+  const size_t NC = (size_t)ntiles_cap;
   unsigned char *b = (unsigned char *)base;
   TileWork w;
   w.counters = (unsigned long long *)b;  // 8-byte aligned first
   b += 64;
   w.ctrl = (unsigned *)b;
   b += 256;
+  w.grids = (TGrid *)b;  // 8-byte aligned
+  b += (size_t)n_grids * sizeof(TGrid);
+  w.gupd = (unsigned long long *)b;
+  b += (size_t)n_grids * 8;
   w.tstate = (unsigned *)b;
-  b += NT * 4;
+  b += NC * 4;
   w.visits = (unsigned *)b;
-  b += NT * 4;
+  b += NC * 4;
   w.queued = (unsigned *)b;
-  b += NT * 4;
+  b += NC * 4;
   w.key = (unsigned *)b;
-  b += NT * 8;
+  b += NC * 8;
   w.list = (int *)b;
-  b += NT * 4 * kSlots;
+  b += NC * 4 * kSlots;
+  w.tile_grid = (int *)b;
+  b += NC * 4;
   w.halo = (float *)b;
+  (void)ts;
   return w;
 }
 
@@ -560,41 +734,44 @@ static rf_status launch_solve(TileArgs &a, int num_sms, cudaStream_t s) {
                                                  dim3(kTileCta), args, smem, s));
 }
 
-rf_status tiles_launch(int num_sms, int ny, int nx, int ts, float h, float eps, const float *proj5,
-                       const uint8_t *src, float *T, float *Tb, int warm, int max_sweeps, float tol, float rtol,
-                       float window, const TileWork &w, const LaunchCtl &ctl, cudaStream_t s) {
+rf_status tiles_launch(const TileLaunch &L, const TileWork &w, const LaunchCtl &ctl, cudaStream_t s) {
+  const int ts = L.ts;
   TileArgs a;
-  a.ny = ny;
-  a.nx = nx;
+  a.n_grids = L.n_grids;
   a.ts = ts;
-  a.tny = (ny + ts - 1) / ts;
-  a.tnx = (nx + ts - 1) / ts;
-  a.ntiles = a.tny * a.tnx;
-  a.h = h;
-  a.eps = eps;
-  a.f = proj5;
-  a.src = src;
-  a.T[0] = T;
-  a.T[1] = Tb;
-  a.tol = tol;
-  a.rtol = rtol;
-  a.window = window > 0.0f ? window : (ts == 32 ? 2.0f : 4.0f);
-  a.warm = warm;
+  a.ntiles_cap = L.ntiles_cap;
+  a.plane = L.total_nodes;
+  a.eps = L.eps;
+  a.f = L.proj5;
+  a.src = L.src;
+  a.T[0] = L.T;
+  a.T[1] = L.Tb;
+  a.tol = L.tol;
+  a.rtol = L.rtol;
+  a.window = L.window > 0.0f ? L.window : (ts == 32 ? 2.0f : 4.0f);
+  a.warm = L.warm;
   // a sweep moves information across the grid, a round across one tile
-  a.max_rounds = max_sweeps * std::max(a.tny, a.tnx);
+  a.max_rounds = L.max_sweeps * std::max(1, (L.max_line + ts - 1) / ts);
   a.max_local = 16 * ts;
   a.w = w;
   a.ctl = ctl;
   if (cudaMemsetAsync(w.counters, 0, 64 + 256, s) != cudaSuccess) return RF_ERR_CUDA;
-  float *esum = (float *)(w.ctrl + kCtrlEsum);
-  const long long n = (long long)ny * nx;
-  const int blocks = blocks_for(std::max(n, (long long)a.ntiles * (4 * ts + 4)), 256, num_sms * 8);
-  tile_seed_kernel<<<blocks, 256, 0, s>>>(a, esum);
-  tile_queue_kernel<<<blocks, 256, 0, s>>>(a);
-  tile_finish_seed_kernel<<<1, 32, 0, s>>>(a, esum);
-  const rf_status rs = ts == 32 ? launch_solve<32>(a, num_sms, s) : launch_solve<16>(a, num_sms, s);
+  if (L.descs) {
+    tile_plan_batch_kernel<<<1, 1024, 0, s>>>(w, L.descs, L.n_grids, ts, L.total_nodes, L.max_line, L.ntiles_cap,
+                                              ctl.st);
+    tile_map_kernel<<<dim3(std::max(1, std::min(64, L.ntiles_cap / 256 + 1)), L.n_grids), 256, 0, s>>>(w);
+  } else {
+    tile_plan_single_kernel<<<1, 32, 0, s>>>(w, L.ny, L.nx, L.h, ts);
+  }
+  const long long per_grid = std::max<long long>(1, L.total_nodes / L.n_grids);
+  const int reset_blocks = blocks_for((long long)L.ntiles_cap * (4 * ts + 4), 256, L.num_sms * 8);
+  tile_reset_kernel<<<reset_blocks, 256, 0, s>>>(a);
+  const int gx = std::max(1, std::min(blocks_for(per_grid, 256, L.num_sms * 8), 65535));
+  tile_seed_kernel<<<dim3(gx, L.n_grids), 256, 0, s>>>(a);
+  tile_finish_seed_kernel<<<blocks_for(L.n_grids, 256, 64), 256, 0, s>>>(a);
+  const rf_status rs = ts == 32 ? launch_solve<32>(a, L.num_sms, s) : launch_solve<16>(a, L.num_sms, s);
   if (rs != RF_OK) return rs;
-  tile_stats_kernel<<<1, 32, 0, s>>>(w.counters, ctl.st, n);
+  tile_stats_kernel<<<blocks_for(L.n_grids, 256, 64), 256, 0, s>>>(a, ctl.st, L.grid_status, 0);
   return cuda_status(cudaGetLastError());
 }
 

@@ -1,5 +1,5 @@
 // rf_sweep_tiles.h -- internal interface of the tile-queue forward solve
-// (rf_sweep_tiles.cu), used by rf_sweep_forward.
+// (rf_sweep_tiles.cu), used by rf_sweep_forward and rf_batch_solve.
 #pragma once
 
 #include "rf_ctx.h"
@@ -7,30 +7,71 @@
 
 namespace rf {
 
+// Per-grid tile geometry (device, written by the plan kernels).
+struct TGrid {
+  long long node_off;  // first node of the grid in the packed arrays
+  int ny, nx;          // grid shape
+  int tny, tnx;        // tiles along y and x
+  int tile_off;        // first tile of the grid
+  float h;             // spacing
+  float inv_scale;     // 1 / (tile side x mean edge cost): keys in tile crossings
+  float esum;          // sum of the edge costs (seed)
+  int has_src;         // the grid holds a source node
+  int pad;
+};
+
 // Per-solve workspace of the tile queue (one device allocation, carved).
 struct TileWork {
   unsigned long long *counters;  // [0] node updates, [1] warp evaluations
-  unsigned *ctrl;                // round slots (count, grab, kmin, pad) x 3, mean edge cost, its sum
+  unsigned *ctrl;                // round slots (count, grab, kmin, pad) x 3, tile count, spare, moved [3]
+  TGrid *grids;                  // [grids]
+  unsigned long long *gupd;      // [grids] node updates per grid
   unsigned *tstate;              // per tile: (round last written << 1) | buffer parity
   unsigned *visits;              // per tile: visits so far
   unsigned *queued;              // per tile: last round it was queued for
-  unsigned *key;                 // [2][tiles] float bits of the queue key, by round parity
-  int *list;                     // [3][tiles] queued tiles, by round mod 3
-  float *halo;                   // [tiles][4 * ts + 4] halo seen at the previous visit
+  unsigned *key;                 // [2][tiles cap] float bits of the queue key, by round parity
+  int *list;                     // [3][tiles cap] queued tiles, by round mod 3
+  int *tile_grid;                // [tiles cap] grid of each tile (batches)
+  float *halo;                   // [tiles cap][4 * ts + 4] halo seen at the previous visit
 };
+
+// What one tile-queue solve needs (a single grid: descs = NULL and ny, nx,
+// h; a batch: the device descriptors and max_line).
+struct TileLaunch {
+  int num_sms;
+  int ts;                        // tile side, 16 or 32
+  int n_grids;
+  const rf_batch_desc *descs;    // batch descriptors (device) or NULL
+  int ny, nx;                    // single grid
+  float h;                       // single grid
+  int max_line;                  // max over grids of max(ny, nx)
+  long long total_nodes;
+  int ntiles_cap;
+  float eps;
+  const float *proj5;
+  const uint8_t *src;
+  float *T, *Tb;
+  int warm, max_sweeps;
+  float tol, rtol, window;
+  int *grid_status;              // batch: [3 * grids] status, forward sweep equivalent (adjoint left alone)
+};
+
+// Initial state of a solve (rf_sweep.cu): T = 0 on sources, +inf elsewhere
+// (cold) or the caller's guess (warm); *has_src |= 1 when a source exists.
+void init_state(float *T, const uint8_t *src, long long n, int warm, DevState *st, int *has_src, int num_sms,
+                cudaStream_t s);
 
 // Tile side used for a requested one (0 or < 32: 16; >= 32: 32).
 int tile_side(int requested);
-int tiles_count(int ny, int nx, int ts);
-size_t tile_work_bytes(int ny, int nx, int ts);
-TileWork tile_work_carve(void *base, int ny, int nx, int ts);
+// Upper bound of the tile count of a batch (exact for one grid up to edge
+// tiles).
+int tiles_cap(int n_grids, long long total_nodes, int max_line, int ts);
+size_t tile_work_bytes(int n_grids, int ntiles_cap, int ts);
+TileWork tile_work_carve(void *base, int n_grids, int ntiles_cap, int ts);
 
-// Seed the queue and run the whole solve in one cooperative launch.  T holds
-// the initial state (init_kernel) and receives the result; Tb is a second
-// buffer of ny * nx floats.  ts: tile side (16 or 32); window:
-// delta-stepping window in tile crossings (<= 0: 2).
-rf_status tiles_launch(int num_sms, int ny, int nx, int ts, float h, float eps, const float *proj5,
-                       const uint8_t *src, float *T, float *Tb, int warm, int max_sweeps, float tol, float rtol,
-                       float window, const TileWork &w, const LaunchCtl &ctl, cudaStream_t s);
+// Plan and seed the queue, then run the whole solve in one cooperative
+// launch.  T holds the initial state (init_kernel) and receives the result;
+// Tb is a second buffer of total_nodes floats.
+rf_status tiles_launch(const TileLaunch &L, const TileWork &w, const LaunchCtl &ctl, cudaStream_t s);
 
 }  // namespace rf

@@ -112,10 +112,41 @@ def local_error(T_gpu, T_orc):
     return np.max([p[1 + di:1 + di + ny, 1 + dj:1 + dj + nx] for di in (-1, 0, 1) for dj in (-1, 0, 1)], axis=0)
 
 
-def stencil_compare(gpu_id, gpu_w1, orc_rec, tmax, T_gpu=None, T_orc=None):
+_DX = (-1, -1, -1, 0, 1, 1, 1, 0)
+_DY = (1, 0, -1, -1, -1, 0, 1, 1)
+
+
+def gpu_choice_is_near_tie(i, j, gid, T_orc, proj, h, eps, bound):
+    """The GPU's stencil at node (i, j), evaluated by the oracle's FP64 local
+    update at the oracle's T: a near-tie when it is geometrically valid
+    (real root, barycentric weights >= 0), its donors precede its value up
+    to `bound` (the causality test can flip within the forward error), and
+    its value is within `bound` of the oracle's best.  The oracle's margin
+    only counts candidates valid at its own T, so a candidate rejected by a
+    hair never enters it."""
+    ny, nx = T_orc.shape
+    Tn = np.array([T_orc[i + _DY[n], j + _DX[n]] if 0 <= i + _DY[n] < ny and 0 <= j + _DX[n] < nx else np.inf
+                   for n in range(8)])
+    l11, l21, l22, wx, wy = (float(proj[c, i, j]) for c in range(5))
+    c = O.cell_eval(Tn, h, l11 * l11 + eps, l11 * l21, l21 * l21 + l22 * l22 + eps, wx, wy)
+    k = int(gid) & 7
+    if (int(gid) & 0xF0) == 0x20:
+        val = c["two"][k]
+        ok = np.isfinite(val) and (c["lam"][k] >= 0).all() and max(Tn[k], Tn[(k + 1) & 7]) < val + bound
+    elif (int(gid) & 0xF0) == 0x10:
+        val = c["one"][k]
+        ok = bool(c["one_ok"][k]) and Tn[k] < val + bound
+    else:
+        return False
+    return bool(ok and val <= T_orc[i, j] + bound)
+
+
+def stencil_compare(gpu_id, gpu_w1, orc_rec, tmax, T_gpu=None, T_orc=None, fields=None):
     """(flips, hard): flips = canonical stencils differ; hard = flips that
     are not near-ties of the oracle (must be empty).  With both T given, the
-    near-tie margin includes twice the local forward error."""
+    near-tie margin includes twice the local forward error; with fields =
+    (proj5 FP64, h, eps) as well, a remaining mismatch is re-examined with
+    the oracle's own local update (gpu_choice_is_near_tie)."""
     a = canonical_stencil(gpu_id, gpu_w1)
     b = canonical_stencil(orc_rec["id"], orc_rec["w1"])
     flips = a != b
@@ -123,6 +154,12 @@ def stencil_compare(gpu_id, gpu_w1, orc_rec, tmax, T_gpu=None, T_orc=None):
     if T_gpu is not None and T_orc is not None:
         bound = bound + 2.0 * local_error(T_gpu, T_orc)
     hard = flips & (orc_rec["margin"] >= bound)
+    if fields is not None and T_orc is not None and hard.any():
+        proj, h, eps = fields
+        bnd = np.broadcast_to(bound, hard.shape)
+        for i, j in np.argwhere(hard):
+            if gpu_choice_is_near_tie(i, j, gpu_id[i, j], T_orc, proj, h, eps, float(bnd[i, j])):
+                hard[i, j] = False
     return flips, hard
 
 

@@ -67,7 +67,8 @@ def test_record_parity(case):
     name, c, gpu, orc = case
     T = orc["T"]
     tmax = T[np.isfinite(T)].max()
-    flips, hard = stencil_compare(gpu["rec_np"]["id"], gpu["rec_np"]["w1"], orc["rec"], tmax, gpu["T"], T)
+    flips, hard = stencil_compare(gpu["rec_np"]["id"], gpu["rec_np"]["w1"], orc["rec"], tmax, gpu["T"], T,
+                                  fields=(orc["proj"], c["h"], c["eps"]))
     raw_diff = gpu["rec_np"]["id"] != orc["rec"]["id"]
     print(f"{name}: ids differ {raw_diff.mean():.4f}, canonical flips {flips.mean():.5f} "
           f"({int(flips.sum())} nodes), hard mismatches {int(hard.sum())}")
