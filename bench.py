@@ -38,15 +38,15 @@ ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-
 # DRAM bytes (read + write) of one launch of the tile-queue forward kernel on the 2048^2 workload (16x16
 # tiles, default window), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).  Reported
 # as roofline.traffic only while the kernel's sources hash to the captured build's.
-TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048): {"sources_sha16": "68f1916a2e265cb7",
-                                                       "bytes": 308641280 + 40726528}}
+TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048): {"sources_sha16": "34a8496fb6f4477c",
+                                                       "bytes": 310743552 + 41989120}}
 TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_00035_gb300/csrc/rf_cone.cuh"]
 # kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
-# source check, then tile queue: seed, queue, finish-seed, solve, stats; streamed: node records + sweep;
-# tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels not
-# counted)
+# source check, then tile queue: plan, reset, seed, finish-seed, solve, stats; streamed: node records +
+# sweep; tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels
+# not counted)
 LAUNCHES_BASE = 3
-LAUNCHES_FORWARD = {8: 7, 2: 4, 1: 3, 4: 3}
+LAUNCHES_FORWARD = {8: 8, 2: 4, 1: 3, 4: 3}
 LAUNCHES_ADJOINT = {"sweep": 1, "ordered": 3}
 
 
