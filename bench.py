@@ -66,9 +66,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched workload in the default run")
-    p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256", "appb2048"],
+    p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256", "appb2048", "adam2048"],
                    help="inverse2048: one 2048^2 grid per step (the headline); batch256: 256 grids of sides "
-                        "64..1024 per step through rf_batch_solve, with the plain per-grid form beside it")
+                        "64..1024 per step through rf_batch_solve, with the plain per-grid form beside it; "
+                        "adam2048: the inverse problem itself, --adam-steps Adam steps through the autograd "
+                        "Function from M = I, w = 0")
+    p.add_argument("--adam-steps", type=int, default=200)
     p.add_argument("--grids", type=int, default=256)
     return p.parse_args()
 
@@ -442,6 +445,10 @@ def batch_measure(grids, steps, warmup, dev, world=1, sampler=None, variant=0):
     from paper_2603_00035_gb300 import replicas
 
     bs = api.BatchSolver(grids, opts=api.make_opts(variant=variant))
+    tuned = None
+    if not variant:
+        from paper_2603_00035_gb300 import autotune
+        tuned = autotune.tune_batch(bs)
     bs.run()
     torch.cuda.synchronize()
     bs.capture()
@@ -489,11 +496,12 @@ def batch_measure(grids, steps, warmup, dev, world=1, sampler=None, variant=0):
     nodes = sum(g["src"].size for g in grids)
     return {"value": rate, "unit": UNIT, "ms_per_batch": total / steps, "grids": len(grids), "nodes": int(nodes),
             "mean_forward_sweep_equivalents": sweeps, "steps": steps, "warmup": warmup,
-            "how": "one CUDA-graph replay of rf_project + rf_batch_solve (tile queue over all grids, record, "
-                   "ordered adjoint over the packed nodes) + rf_project_backward",
+            "how": "one CUDA-graph replay of rf_project + rf_batch_solve + rf_project_backward (variant, tile side "
+                   "and window from the batch autotuner unless given)",
             "plain_form": {"value": plain_rate, "unit": UNIT, "ms_per_batch": plain_ms,
                            "how": "rf_project, rf_sweep_forward, rf_adjoint(ordered), rf_project_backward per grid"},
-            "speedup_vs_plain": rate / plain_rate}
+            "speedup_vs_plain": rate / plain_rate,
+            "autotuned": None if tuned is None else {"band": tuned[0], "variant": tuned[1], "window": tuned[2]}}
 
 
 def run_batch(args):
@@ -619,6 +627,42 @@ def run_appb(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adam(args):
+    """The inverse metric problem at n x n (Sec. 4, Eq. 8): recover the five
+    fields (L11, L21, L22, wx, wy) of a 16-mode ground truth from arrival
+    times observed on 0.5 % of the nodes, with Adam (1e-2 on L, 5e-3 on w)
+    through RFSolve, from M = I, w = 0.  Reports the loss and the relative
+    recovery errors of the metric and the drift."""
+    import torch
+
+    import rf_inputs as R
+    from paper_2603_00035_gb300 import build as B
+    from paper_2603_00035_gb300.inverse import run_inverse
+
+    B.build()
+    torch.cuda.set_device(0)
+    n = args.size
+    c = R.config_inverse(n=n, seed=0)
+    raw_true = torch.from_numpy(c["raw"]).cuda()
+    src = torch.from_numpy(c["src"]).cuda()
+    obs = torch.from_numpy(c["obs"]).cuda()
+    run_inverse(raw_true, src, obs, c["h"], steps=3)  # warm-up: builds, workspace
+    torch.cuda.synchronize()
+    out = run_inverse(raw_true, src, obs, c["h"], steps=args.adam_steps, log_every=max(1, args.adam_steps // 10))
+    hist = out["loss_history"]
+    line = {"metric": f"inverse problem {n}x{n}: Adam steps/s through RFSolve", "value": out["steps"] / out["seconds"],
+            "unit": "steps/s", "n_gpus": 1, "steps": out["steps"], "warmup": 3,
+            "ms_per_step": 1e3 * out["seconds"] / out["steps"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"inverse metric problem {n}x{n}, 16-mode ground truth, 4 sources, "
+                                   f"{100 * c['obs'].mean():.2f} % observed, Adam lr 1e-2 (L) / 5e-3 (w), "
+                                   "initial M = I, w = 0", "steps": out["steps"]},
+            "loss_first": hist[0][1], "loss_last_logged": hist[-1][1], "final_loss": out["final_loss"],
+            "loss_history": hist, "rel_err_metric": out["rel_err_metric"], "rel_err_drift": out["rel_err_drift"],
+            "timing": "wall clock of the whole Adam loop (forward, backward, optimiser), synchronised at the end"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -627,6 +671,8 @@ def main():
         run_batch(args)
     elif args.workload == "appb2048":
         run_appb(args)
+    elif args.workload == "adam2048":
+        run_adam(args)
     else:
         run_ours(args)
 

@@ -36,6 +36,7 @@ def cache_path() -> str:
 
 
 def bucket(ny: int, nx: int) -> int:
+    """Next power of two of max(ny, nx)."""
     m = max(int(ny), int(nx), 1)
     b = 1
     while b < m:
@@ -123,6 +124,61 @@ def tune_sweep(proj5, eps, src, h, candidates=None, repeats=2, force=False):
     best = choose(timings)
     record(name, ny, nx, *best, timings[best],
            {f"{b}x{k}x{n}x{w:g}": round(v, 4) for (b, k, n, w), v in timings.items()})
+    return best
+
+
+# batched solves: (band, variant, window) -- 8 the tile queue over all grids (band = tile side), 1 the
+# persistent line-sweep kernel (whole grids per CTA)
+BATCH_CANDIDATES = [(16, 8, 0.0), (16, 8, 2.0), (16, 8, 8.0), (32, 8, 0.0), (0, 1, 0.0)]
+
+
+def batch_key(n_grids: int, total_nodes: int) -> str:
+    return f"batch{int(n_grids)}x{bucket(int(total_nodes), 1)}"
+
+
+def tune_batch(bs, candidates=None, repeats=2, force=False):
+    """Time BatchSolver `bs` (api.BatchSolver, not yet captured) with each
+    candidate (band, variant, window), cache and return the fastest; leaves
+    bs.opts set to it.  Uses the cached result unless force."""
+    import torch
+
+    from . import api
+
+    name = torch.cuda.get_device_name(bs.T.device)
+    key = batch_key(bs.n, bs.total)
+    if not force:
+        with _lock:
+            e = _load().get(name, {}).get(key)
+        if e and "variant" in e:
+            best = (int(e["band"]), int(e["variant"]), float(e.get("window", 0.0)))
+            bs.opts = api.make_opts(band=best[0], variant=best[1], window=best[2])
+            return best
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timings = {}
+    for cand in (candidates or BATCH_CANDIDATES):
+        band, variant = cand[0], cand[1]
+        window = cand[2] if len(cand) > 2 else 0.0
+        bs.opts = api.make_opts(band=band, variant=variant, window=window)
+        try:
+            bs.run()
+        except Exception:
+            continue  # not supported for this batch (e.g. lines beyond the persistent kernel's limit)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(repeats):
+            bs.run()
+        e1.record()
+        torch.cuda.synchronize()
+        timings[(band, variant, window)] = e0.elapsed_time(e1) / repeats
+    api.Context.get(bs.T.device).stats()
+    best = choose(timings)
+    bs.opts = api.make_opts(band=best[0], variant=best[1], window=best[2])
+    with _lock:
+        d = _load()
+        d.setdefault(name, {})[key] = {"band": best[0], "variant": best[1], "window": best[2], "block": 0,
+                                        "ms": timings[best],
+                                        "timings": {f"{b}x{v}x{w:g}": round(t, 4) for (b, v, w), t in timings.items()}}
+        _store(d)
     return best
 
 

@@ -186,6 +186,79 @@ def solve(net, raw5, src, h, eps=1e-6, delta=0.05, opts=None, residual_tol=None,
     return T, info
 
 
+def clear_underestimates(proj, src, h, T, eps=1e-6, ctx=None):
+    """Set to +inf every node of the guess T whose value lies below the
+    minimum of its valid candidates at T (residual < 0): such a value cannot
+    be reached from its neighbours and would otherwise have to rise one edge
+    cost per update.  Returns the number of nodes cleared."""
+    mx, res = api.rf_residual(proj, eps, src, h, T, per_node=True, ctx=ctx)
+    bad = (res < 0) & (src == 0)
+    T.masked_fill_(bad, float("inf"))
+    return int(bad.sum())
+
+
+def compare(net, raw5, src, h, eps=1e-6, delta=0.05, inflate=1.1, loose=1e-4):
+    """Cold and warm solves of one grid with the tile queue, timed with CUDA
+    events: the exact solve (rtol 1e-6) cold from +inf, the same with a
+    stopping tolerance of `loose`, and warm starts from the network's guess
+    (inflated, and inflated with the underestimates cleared) at both
+    tolerances; errors are max |T - T_cold exact| / max T.  The guess's own
+    cost (network + resampling) is reported apart."""
+    ctx = net.ctx
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    proj, _ = api.rf_project(raw5, eps, delta)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def solve(T, rtol, warm):
+        o = api.make_opts(rtol=rtol, warm=warm, max_sweeps=1000)
+        api.rf_sweep_forward(proj, eps, src, h, opts=o, T=T, record=False)
+        return T
+
+    T_ref = torch.empty(src.shape, dtype=torch.float32, device=raw5.device)
+    solve(T_ref, 1e-6, False)  # warm-up of the workspace
+    _, ms_cold = timed(lambda: solve(T_ref, 1e-6, False))
+    st_cold = ctx.stats()
+    tmax = float(T_ref[torch.isfinite(T_ref)].max())
+    rows = {"cold_exact": dict(ms=ms_cold, rounds=st_cold["rounds"], updates_per_node=st_cold["cell_updates"] / src.numel(),
+                               err=0.0, status=st_cold["status_name"])}
+
+    def err(T):
+        d = (T - T_ref).abs()
+        d = torch.where(torch.isfinite(T_ref), d, torch.zeros_like(d))
+        return float(d.max()) / tmax
+
+    T = torch.empty_like(T_ref)
+    _, ms = timed(lambda: solve(T, loose, False))
+    st = ctx.stats()
+    rows["cold_loose"] = dict(ms=ms, rounds=st["rounds"], updates_per_node=st["cell_updates"] / src.numel(),
+                              err=err(T), status=st["status_name"])
+    (_, T0), ms_guess = timed(lambda: guess(net, raw5, src, h, eps, delta))
+    rows["guess"] = dict(ms=ms_guess, err=err(T0 * inflate))
+    for clear in (False, True):
+        for rtol, tag in ((1e-6, "exact"), (loose, "loose")):
+            T = (T0 * inflate).contiguous()
+            n_clear = 0
+
+            def run():
+                nonlocal n_clear
+                if clear:
+                    n_clear = clear_underestimates(proj, src, h, T, eps, ctx)
+                return solve(T, rtol, True)
+            _, ms = timed(run)
+            st = ctx.stats()
+            rows[f"warm{'_cleared' if clear else ''}_{tag}"] = dict(
+                ms=ms, rounds=st["rounds"], updates_per_node=st["cell_updates"] / src.numel(), err=err(T),
+                status=st["status_name"], cleared=n_clear)
+    return rows
+
+
 def main():
     import argparse
     import json
@@ -204,28 +277,17 @@ def main():
     net, tr = train(samples=a.samples, log=lambda m: print(m, file=sys.stderr, flush=True))
     if a.save:
         torch.save(net.state_dict(), a.save)
-    rows = []
     n = a.eval_n
     h = 1.0 / (n - 1)
+    evals = []
     for k in range(a.eval_grids):
         raw = torch.from_numpy(R.randers_fields(n, n, h, 16, 900 + k, omega="unit", omega_scale=0.3)).cuda()
         src = torch.from_numpy(R.random_sources(n, n, 1 + (k % 8), 900 + k)).cuda()
-        ctx = net.ctx
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        proj, _ = api.rf_project(raw, 1e-6, 0.05)
-        Tc, _ = api.rf_sweep_forward(proj, 1e-6, src, h, record=False)
-        stc = ctx.stats()
-        torch.cuda.synchronize()
-        tc = time.perf_counter() - t0
-        Tw, info = solve(net, raw, src, h)
-        err = float((Tw - Tc).abs().max() / Tc.max())
-        rows.append(dict(grid=n, sources=int(src.sum()), cold_sweeps=stc["sweeps"], cold_s=tc,
-                         warm_sweeps=info["warm_sweeps"], warm_s=info["seconds"], fallback=info["fallback"],
-                         residual=info["residual"], max_rel_diff_warm_vs_cold=err))
+        evals.append(dict(grid=n, sources=int(src.sum()), **compare(net, raw, src, h)))
+        print(json.dumps(evals[-1]), file=sys.stderr, flush=True)
     print(json.dumps(dict(train=dict(samples=tr["samples"], seconds=tr["seconds"],
                                      loss_first=tr["loss_history"][0], loss_last=float(np.mean(tr["loss_history"][-20:]))),
-                          eval=rows)))
+                          eval=evals)))
 
 
 if __name__ == "__main__":

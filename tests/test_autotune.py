@@ -56,3 +56,10 @@ def test_candidates_are_accepted_shapes():
         assert band + 2 * block <= (128 if variant == 4 else 96)
         if variant == 2:
             assert (band, block) in {(32, 32), (64, 16), (32, 16), (16, 16)}
+
+
+def test_batch_candidates_and_key():
+    # tile queue (variant 8) with tile side 16 or 32, or the persistent kernel (variant 1)
+    for band, variant, window in A.BATCH_CANDIDATES:
+        assert (variant == 8 and band in (16, 32) and window >= 0.0) or (variant == 1 and window == 0.0)
+    assert A.batch_key(256, 62834981) == "batch256x67108864"

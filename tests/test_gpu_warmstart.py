@@ -93,3 +93,28 @@ def test_warm_solve_without_fallback_matches_oracle():
     err = np.abs(Tw[fin] - To[fin]).max()
     print(f"warm 1024^2: sweeps {info['warm_sweeps']}, max |dT| / max T = {err / To[fin].max():.2e}")
     assert err <= FWD_TOL * To[fin].max()
+
+
+def test_warm_and_cold_time_to_accuracy_measured():
+    """Cold and warm starts of a 1024^2 solve with the tile queue, at the
+    exact tolerance (rtol 1e-6) and at a 1e-4 stopping tolerance: every run
+    ends at the cold solution to within 1e-4 max T, and the warm/cold time
+    ratio at 1e-4 accuracy is measured and printed (a briefly trained network:
+    the ratio is whatever it is -- the test pins that it is measured and
+    finite, and that no run breaks the accuracy)."""
+    net, _ = WS.train(samples=64, chunk=64, batch=8)
+    n = 1024
+    h = 1.0 / (n - 1)
+    raw = torch.from_numpy(R.randers_fields(n, n, h, 16, 79, omega="unit", omega_scale=0.3)).cuda()
+    src = torch.from_numpy(R.random_sources(n, n, 3, 79)).cuda()
+    rows = WS.compare(net, raw, src, h)
+    for name, r in rows.items():
+        if name == "guess":
+            continue
+        assert r["status"] == "RF_OK", (name, r)
+        assert r["err"] <= FWD_TOL, (name, r)
+    ratio = (rows["warm_loose"]["ms"] + rows["guess"]["ms"]) / rows["cold_loose"]["ms"]
+    ratio_solve = rows["warm_loose"]["ms"] / rows["cold_loose"]["ms"]
+    print(f"1024^2 at 1e-4: cold {rows['cold_loose']['ms']:.2f} ms, warm {rows['warm_loose']['ms']:.2f} ms "
+          f"+ guess {rows['guess']['ms']:.2f} ms: warm/cold {ratio:.2f} ({ratio_solve:.2f} without the guess)")
+    assert 0.0 < ratio < 50.0
