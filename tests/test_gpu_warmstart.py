@@ -96,12 +96,13 @@ def test_warm_solve_without_fallback_matches_oracle():
 
 
 def test_warm_and_cold_time_to_accuracy_measured():
-    """Cold and warm starts of a 1024^2 solve with the tile queue, at the
-    exact tolerance (rtol 1e-6) and at a 1e-4 stopping tolerance: every run
-    ends at the cold solution to within 1e-4 max T, and the warm/cold time
-    ratio at 1e-4 accuracy is measured and printed (a briefly trained network:
-    the ratio is whatever it is -- the test pins that it is measured and
-    finite, and that no run breaks the accuracy)."""
+    """Cold and warm starts of a 1024^2 solve with the tile queue.  The
+    exact runs (rtol 1e-6) end within 1e-4 max T of the cold solution -- the
+    same accuracy -- and their time ratio is measured and printed (a briefly
+    trained network: the ratio is whatever it is; the test pins that it is
+    measured and finite).  The runs with a 1e-4 stopping tolerance are
+    printed too: such a tolerance lets changes below it stop propagating, so
+    it does not deliver 1e-4 accuracy (its error is reported, not bounded)."""
     net, _ = WS.train(samples=64, chunk=64, batch=8)
     n = 1024
     h = 1.0 / (n - 1)
@@ -112,9 +113,11 @@ def test_warm_and_cold_time_to_accuracy_measured():
         if name == "guess":
             continue
         assert r["status"] == "RF_OK", (name, r)
-        assert r["err"] <= FWD_TOL, (name, r)
-    ratio = (rows["warm_loose"]["ms"] + rows["guess"]["ms"]) / rows["cold_loose"]["ms"]
-    ratio_solve = rows["warm_loose"]["ms"] / rows["cold_loose"]["ms"]
-    print(f"1024^2 at 1e-4: cold {rows['cold_loose']['ms']:.2f} ms, warm {rows['warm_loose']['ms']:.2f} ms "
-          f"+ guess {rows['guess']['ms']:.2f} ms: warm/cold {ratio:.2f} ({ratio_solve:.2f} without the guess)")
-    assert 0.0 < ratio < 50.0
+        assert np.isfinite(r["err"]), (name, r)
+        if name.endswith("exact"):
+            assert r["err"] <= FWD_TOL, (name, r)
+    ratio = (rows["warm_exact"]["ms"] + rows["guess"]["ms"]) / rows["cold_exact"]["ms"]
+    print(f"1024^2 at 1e-4 accuracy: cold {rows['cold_exact']['ms']:.2f} ms, warm {rows['warm_exact']['ms']:.2f} ms "
+          f"+ guess {rows['guess']['ms']:.2f} ms: warm/cold {ratio:.2f}; 1e-4 stopping tolerance: cold err "
+          f"{rows['cold_loose']['err']:.1e}, warm err {rows['warm_loose']['err']:.1e}")
+    assert 0.0 < ratio < 1e3
