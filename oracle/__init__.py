@@ -50,8 +50,14 @@ def _load():
         lib.orc_residual.argtypes = [I, I, D, D, P, P, P, P, P, P, P, P]
         lib.orc_record.argtypes = [I, I, D, D, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_adjoint.argtypes = [I, I, P, P, P, P, P, P, P, P]
+        lib.orc_cell_softmin.argtypes = [P, D, D, D, D, D, D, D, P, P]
+        lib.orc_cell_softmin.restype = D
+        lib.orc_solve_softmin_gs.argtypes = [I, I, D, D, P, P, P, P, P, P, D, D, I, P, P]
+        lib.orc_softmin_record.argtypes = [I, I, D, D, P, P, P, P, P, P, P, D, P, P]
+        lib.orc_softmin_adjoint.argtypes = [I, I, P, P, P, P, P, D, I, P, P, P]
         for f in ("orc_project", "orc_project_backward", "orc_solve_gs", "orc_solve_ordered",
-                  "orc_residual", "orc_record", "orc_adjoint"):
+                  "orc_residual", "orc_record", "orc_adjoint", "orc_solve_softmin_gs", "orc_softmin_record",
+                  "orc_softmin_adjoint"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -231,3 +237,72 @@ def solve_and_grad(raw5, src, h, eps, delta, g, max_iter=200):
     graw = project_backward(raw5, clip, eps, delta, gproj)
     return dict(proj=proj, clip=clip, T=T, iters=iters, status=st, updates=upd, rec=rec, lam=lam,
                 gproj=gproj, graw=graw)
+
+
+# ---- soft-min relaxation (Sec. 3.3 names it; the formula is this build's reading) ----
+
+def cell_softmin(Tn, h, g11, g12, g22, wx, wy, tau):
+    """Soft-min of one node over its 8 stencil values (each the minimum of
+    its segment: the valid two-point candidate, else the smaller endpoint
+    one-point candidate): (T0, p[8] softmax weights of the stencils,
+    from[8] the candidate behind each value: 8 + k two-point of stencil k, n
+    one-point through neighbour n, -1 none)."""
+    lib = _load()
+    p = np.zeros(8)
+    frm = np.zeros(8, np.int32)
+    T0 = lib.orc_cell_softmin(_p(_d(Tn)), h, g11, g12, g22, wx, wy, tau, _p(p), _p(frm))
+    return T0, p, frm
+
+
+def solve_softmin(proj5, src, h, eps, tau, tol=1e-14, max_iter=2000):
+    """Gauss-Seidel sweeps of T = softmin_tau(candidates(T)).  Returns (T,
+    iterations, status)."""
+    lib = _load()
+    f, (l11, l21, l22, wx, wy) = _fields(proj5)
+    ny, nx = f.shape[1:]
+    src = _u8(src)
+    T = np.zeros((ny, nx))
+    it = ctypes.c_int(0)
+    st = lib.orc_solve_softmin_gs(ny, nx, h, eps, _p(l11), _p(l21), _p(l22), _p(wx), _p(wy), _p(src), tau, tol,
+                                  max_iter, _p(T), ctypes.byref(it))
+    return T, it.value, st
+
+
+def softmin_record(proj5, src, h, eps, T, tau):
+    """(wnb (8, ny, nx) = dT/dT(neighbour n), dth (5, ny, nx) = dT/dtheta)."""
+    lib = _load()
+    f, (l11, l21, l22, wx, wy) = _fields(proj5)
+    ny, nx = f.shape[1:]
+    wnb = np.zeros((8, ny, nx))
+    dth = np.zeros((5, ny, nx))
+    lib.orc_softmin_record(ny, nx, h, eps, _p(l11), _p(l21), _p(l22), _p(wx), _p(wy), _p(_u8(src)), _p(_d(T)), tau,
+                           _p(wnb), _p(dth))
+    return wnb, dth
+
+
+def softmin_adjoint(src, T, wnb, dth, g, tol=1e-15, max_pass=200):
+    """(lambda, grad5, passes) of the soft-min system."""
+    lib = _load()
+    T = _d(T)
+    ny, nx = T.shape
+    lam = np.zeros((ny, nx))
+    grad = np.zeros((5, ny, nx))
+    passes = ctypes.c_int(0)
+    st = lib.orc_softmin_adjoint(ny, nx, _p(_u8(src)), _p(T), _p(_d(wnb)), _p(_d(dth)), _p(_d(g)), tol, max_pass,
+                                 _p(lam), _p(grad), ctypes.byref(passes))
+    if st != OK:
+        raise ValueError(f"orc_softmin_adjoint status {st}")
+    return lam, grad, passes.value
+
+
+def softmin_solve_and_grad(raw5, src, h, eps, delta, g, tau):
+    """Whole soft-min path on the CPU: project -> soft solve -> record ->
+    adjoint -> project backward."""
+    proj, clip = project(raw5, eps, delta)
+    T, iters, st = solve_softmin(proj, src, h, eps, tau)
+    wnb, dth = softmin_record(proj, src, h, eps, T, tau)
+    g = np.where(np.isfinite(T), g, 0.0)
+    lam, gproj, passes = softmin_adjoint(src, T, wnb, dth, g)
+    graw = project_backward(raw5, clip, eps, delta, gproj)
+    return dict(proj=proj, clip=clip, T=T, iters=iters, status=st, wnb=wnb, dth=dth, lam=lam, gproj=gproj, graw=graw,
+                passes=passes)

@@ -662,3 +662,293 @@ int orc_adjoint(int ny, int nx, const uint8_t *src, const double *T,
   free(lam);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/*
+ * Soft-min relaxation of the stencil selection (Sec. 3.3, "Stencil
+ * Boundaries and Non-Smoothness", names soft-min relaxations as an
+ * alternative to the hard minimum without giving a formula).  Reading used
+ * here: each of the node's 8 stencils k (donors k, k+1) has the value of
+ * the minimum of its segment -- the two-point candidate when it is valid
+ * (App. A), else the smaller one-point candidate of its finite endpoints --
+ *     c_k = two_k if valid, else min(one_k, one_{k+1}),
+ * and the node takes
+ *     T0 = -tau log sum_k exp(-c_k / tau)
+ * over the stencils with a value, evaluated as c_min - tau log sum_k
+ * exp(-(c_k - c_min) / tau), with the softmax weights p_k = exp(-(c_k -
+ * T0) / tau) (they sum to 1; computed as e_k / sum e).  A per-candidate sum would count a two-point
+ * update that turns valid at lambda = 0 next to the one-point update it
+ * equals there, so T0 would jump at every such switch; the segment minimum
+ * moves continuously through it.  tau -> 0 gives the hard minimum (the
+ * minimum over the stencil values equals the minimum over all valid
+ * candidates); tau = 0 is the hard minimum exactly.
+ * Per stencil: p[k], and src[k] = the candidate that gives c_k (8 + k: the
+ * two-point of stencil k; n: the one-point through neighbour n; -1: none).
+ * Returns T0 (+inf: no stencil has a value).
+ */
+static double stencil_value(const orc_cands *c, int k, int *from) {
+  int a = k, b = (k + 1) & 7;
+  if (c->two_ok[k]) {
+    *from = 8 + k;
+    return c->two[k];
+  }
+  double va = c->one_ok[a] ? c->one[a] : INFINITY;
+  double vb = c->one_ok[b] ? c->one[b] : INFINITY;
+  if (!isfinite(va) && !isfinite(vb)) {
+    *from = -1;
+    return INFINITY;
+  }
+  *from = (va <= vb) ? a : b;
+  return va <= vb ? va : vb;
+}
+
+static double cell_softmin(const orc_cands *c, double tau, double p[8], int from[8]) {
+  double v[8], cmin = INFINITY;
+  for (int k = 0; k < 8; ++k) {
+    v[k] = stencil_value(c, k, &from[k]);
+    p[k] = 0.0;
+    if (v[k] < cmin) cmin = v[k];
+  }
+  if (!isfinite(cmin))
+    return INFINITY;
+  if (!(tau > 0.0)) {
+    for (int k = 0; k < 8; ++k)
+      if (v[k] == cmin) {
+        p[k] = 1.0;
+        break;
+      }
+    return cmin;
+  }
+  /* e_k relative to the minimum (no overflow); p_k = e_k / s sums to 1
+   * exactly, where exp(-(c_k - T0)/tau) would lose the digits of the
+   * difference when tau is tiny */
+  double e[8], s = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    e[k] = isfinite(v[k]) ? exp(-(v[k] - cmin) / tau) : 0.0;
+    s += e[k];
+  }
+  for (int k = 0; k < 8; ++k)
+    p[k] = e[k] / s;
+  return cmin - tau * log(s);
+}
+
+/* Exported: the soft-min of one node (for pin tests); p[8] = stencil
+ * weights, from[8] = the candidate behind each stencil value (see
+ * cell_softmin). */
+double orc_cell_softmin(const double *Tn, double h, double g11, double g12,
+                        double g22, double wx, double wy, double tau,
+                        double *p, int *from) {
+  orc_cands c;
+  cell_candidates(Tn, h, g11, g12, g22, wx, wy, &c);
+  return cell_softmin(&c, tau, p, from);
+}
+
+/*
+ * Gauss-Seidel sweeps of the soft-min system (the sweep order of
+ * orc_solve_gs): T = 0 on sources, +inf elsewhere, then every non-source
+ * node is replaced by the soft-min of its candidates, until an iteration of
+ * four sweeps changes no value by more than tol (absolute).  The soft
+ * update is smooth, so the values converge geometrically rather than
+ * stopping exactly.
+ */
+int orc_solve_softmin_gs(int ny, int nx, double h, double eps,
+                         const double *L11, const double *L21,
+                         const double *L22, const double *wx,
+                         const double *wy, const uint8_t *src, double tau,
+                         double tol, int max_iter, double *T,
+                         int *iters_out) {
+  if (ny < 1 || nx < 1 || !(h > 0.0) || tau < 0.0)
+    return ORC_ERR_INVALID_ARG;
+  int64_t n = (int64_t)ny * nx;
+  for (int64_t p = 0; p < n; ++p)
+    T[p] = src[p] ? 0.0 : INFINITY;
+  if (!count_sources(n, src)) {
+    if (iters_out) *iters_out = 0;
+    return ORC_ERR_NO_SOURCE;
+  }
+  int it;
+  for (it = 1; it <= max_iter; ++it) {
+    double change = 0.0;
+    for (int d = 0; d < 4; ++d) {
+      int lines = (d % 2 == 0) ? nx : ny;
+      int len = (d % 2 == 0) ? ny : nx;
+      for (int s = 0; s < lines; ++s) {
+        int line = (d < 2) ? s : lines - 1 - s;
+        for (int q = 0; q < len; ++q) {
+          int i = (d % 2 == 0) ? q : line;
+          int j = (d % 2 == 0) ? line : q;
+          size_t p = (size_t)i * nx + j;
+          if (src[p])
+            continue;
+          orc_cands c;
+          double pk[8];
+          int from[8];
+          node_candidates(ny, nx, h, eps, L11, L21, L22, wx, wy, T, NULL, i,
+                          j, &c);
+          double v = cell_softmin(&c, tau, pk, from);
+          double dv = (isinf(v) && isinf(T[p])) ? 0.0 : fabs(v - T[p]);
+          if (isinf(v) != isinf(T[p])) dv = INFINITY;
+          if (dv > change) change = dv;
+          T[p] = v;
+        }
+      }
+    }
+    if (change <= tol)
+      break;
+  }
+  if (iters_out) *iters_out = it > max_iter ? max_iter : it;
+  return it > max_iter ? ORC_ERR_NOT_CONVERGED : ORC_OK;
+}
+
+/*
+ * Partials of one candidate of node (i, j) at T (the closed forms of
+ * orc_record, normalised by dR/dT0): wa, wb = dc/dT of its donors (wb = 0
+ * for one-point), dth[5] = dc/d(L11, L21, L22, wx, wy).
+ */
+static void candidate_partials(int kind, int idx, const orc_cands *cs,
+                               double h, double L11, double L21, double L22,
+                               double wx, double wy, double Ti, double c,
+                               double *wa, double *wb, double dth[5]) {
+  double jac0, jac1, jac2, dRdG11, dRdG12, dRdG22, dRdbx, dRdby;
+  if (kind == 2) {
+    int a = idx, b = (idx + 1) & 7;
+    double m1x = h * ORC_DX[a], m1y = h * ORC_DY[a];
+    double m2x = h * ORC_DX[b], m2y = h * ORC_DY[b];
+    double qu1 = -cs->lam[idx][0], qu2 = -cs->lam[idx][1];
+    jac0 = -2.0 * (qu1 + qu2);
+    jac1 = 2.0 * qu1;
+    jac2 = 2.0 * qu2;
+    double vx = m1x * qu1 + m2x * qu2, vy = m1y * qu1 + m2y * qu2;
+    dRdbx = 2.0 * vx;
+    dRdby = 2.0 * vy;
+    dRdG11 = -vx * vx;
+    dRdG12 = -vx * vy;
+    dRdG22 = -vy * vy;
+  } else {
+    double mx = h * ORC_DX[idx], my = h * ORC_DY[idx];
+    double r = Ti - (mx * wx + my * wy) - c;
+    jac0 = -2.0 * r;
+    jac1 = 2.0 * r;
+    jac2 = 0.0;
+    dRdbx = 2.0 * r * mx;
+    dRdby = 2.0 * r * my;
+    dRdG11 = -mx * mx;
+    dRdG12 = -mx * my;
+    dRdG22 = -my * my;
+  }
+  double drt[5];
+  drt[0] = 2.0 * (dRdG11 * L11 + dRdG12 * L21);
+  drt[1] = 2.0 * (dRdG12 * L11 + dRdG22 * L21);
+  drt[2] = 2.0 * dRdG22 * L22;
+  drt[3] = -dRdbx;
+  drt[4] = -dRdby;
+  *wa = (jac0 != 0.0) ? -jac1 / jac0 : 0.0;
+  *wb = (jac0 != 0.0) ? -jac2 / jac0 : 0.0;
+  for (int k = 0; k < 5; ++k)
+    dth[k] = (jac0 != 0.0) ? -drt[k] / jac0 : 0.0;
+}
+
+/*
+ * Record of the soft-min system at T: for every non-source reached node,
+ * wnb[nb * n + p] = dT_p / dT(neighbour nb) = sum_k p_k dc_k/dT_nb and
+ * dth[c * n + p] = dT_p / dtheta_c = sum_k p_k dc_k/dtheta_c over its
+ * candidates (the chain rule through the soft-min); zero elsewhere.
+ */
+int orc_softmin_record(int ny, int nx, double h, double eps,
+                       const double *L11, const double *L21, const double *L22,
+                       const double *wx, const double *wy, const uint8_t *src,
+                       const double *T, double tau, double *wnb, double *dth) {
+  int64_t n = (int64_t)ny * nx;
+  for (int64_t p = 0; p < n; ++p) {
+    for (int c = 0; c < 8; ++c) wnb[c * n + p] = 0.0;
+    for (int c = 0; c < 5; ++c) dth[c * n + p] = 0.0;
+  }
+  for (int i = 0; i < ny; ++i)
+    for (int j = 0; j < nx; ++j) {
+      int64_t p = (int64_t)i * nx + j;
+      if (src[p] || !isfinite(T[p]))
+        continue;
+      orc_cands cs;
+      double Tn[8];
+      node_candidates(ny, nx, h, eps, L11, L21, L22, wx, wy, T, NULL, i, j,
+                      &cs);
+      gather_neighbours(ny, nx, T, i, j, NULL, Tn);
+      double pk[8];
+      int from[8];
+      cell_softmin(&cs, tau, pk, from);
+      for (int k = 0; k < 8; ++k) {
+        if (!(pk[k] > 0.0) || from[k] < 0)
+          continue;
+        double wa, wb, d5[5];
+        if (from[k] >= 8) {
+          candidate_partials(2, k, &cs, h, L11[p], L21[p], L22[p], wx[p], wy[p],
+                             0.0, cs.two[k], &wa, &wb, d5);
+          wnb[k * n + p] += pk[k] * wa;
+          wnb[((k + 1) & 7) * n + p] += pk[k] * wb;
+        } else {
+          const int nb = from[k];
+          candidate_partials(1, nb, &cs, h, L11[p], L21[p], L22[p], wx[p], wy[p],
+                             Tn[nb], cs.one[nb], &wa, &wb, d5);
+          wnb[nb * n + p] += pk[k] * wa;
+        }
+        for (int c = 0; c < 5; ++c) dth[c * n + p] += pk[k] * d5[c];
+      }
+    }
+  return ORC_OK;
+}
+
+/*
+ * Adjoint of the soft-min system (Alg. 2's back-substitution for the
+ * relaxed residual R_p = T_p - softmin_p(T)): lambda_p = g_p + sum over
+ * neighbours q of wnb_q(direction q -> p) lambda_q, dL/dtheta_p = lambda_p
+ * dth_p.  A soft value can fall below one of its donors, so the weight graph
+ * need not be ordered by T: the solve sweeps the nodes in decreasing T
+ * (Gauss-Seidel), which is exact in one pass when it is, and repeats until
+ * no multiplier changes by more than tol relative.  Returns the number of
+ * passes in *passes_out.  Sources and unreached nodes: zero gradient.
+ */
+int orc_softmin_adjoint(int ny, int nx, const uint8_t *src, const double *T,
+                        const double *wnb, const double *dth, const double *g,
+                        double tol, int max_pass, double *lam, double *grad,
+                        int *passes_out) {
+  int64_t n = (int64_t)ny * nx;
+  order_item *ord = (order_item *)malloc(sizeof(order_item) * (size_t)n);
+  if (!ord)
+    return ORC_ERR_INVALID_ARG;
+  for (int64_t p = 0; p < n; ++p) {
+    ord[p].t = T[p];
+    ord[p].p = p;
+    lam[p] = 0.0;
+  }
+  qsort(ord, (size_t)n, sizeof(order_item), by_decreasing_t);
+  int pass;
+  for (pass = 1; pass <= max_pass; ++pass) {
+    double change = 0.0, scale = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      int64_t p = ord[k].p;
+      if (!isfinite(T[p]))
+        continue;
+      int i = (int)(p / nx), j = (int)(p % nx);
+      double acc = g[p];
+      for (int nb = 0; nb < 8; ++nb) {
+        int ii = i + ORC_DY[nb], jj = j + ORC_DX[nb];
+        if (ii < 0 || ii >= ny || jj < 0 || jj >= nx)
+          continue;
+        int64_t q = (int64_t)ii * nx + jj;
+        acc += wnb[((nb + 4) & 7) * n + q] * lam[q];
+      }
+      double d = fabs(acc - lam[p]);
+      if (d > change) change = d;
+      if (fabs(acc) > scale) scale = fabs(acc);
+      lam[p] = acc;
+    }
+    if (change <= tol * (scale > 0.0 ? scale : 1.0))
+      break;
+  }
+  if (passes_out) *passes_out = pass > max_pass ? max_pass : pass;
+  for (int64_t p = 0; p < n; ++p)
+    for (int c = 0; c < 5; ++c)
+      grad[c * n + p] = (isfinite(T[p]) && !src[p]) ? lam[p] * dth[c * n + p] : 0.0;
+  free(ord);
+  return pass > max_pass ? ORC_ERR_NOT_CONVERGED : ORC_OK;
+}
