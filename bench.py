@@ -66,11 +66,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched workload in the default run")
-    p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256", "appb2048", "adam2048"],
+    p.add_argument("--workload", default="inverse2048", choices=["inverse2048", "batch256", "appb2048", "adam2048", "softmin"],
                    help="inverse2048: one 2048^2 grid per step (the headline); batch256: 256 grids of sides "
                         "64..1024 per step through rf_batch_solve, with the plain per-grid form beside it; "
                         "adam2048: the inverse problem itself, --adam-steps Adam steps through the autograd "
-                        "Function from M = I, w = 0")
+                        "Function from M = I, w = 0; softmin: the soft-min relaxation (forward, record, adjoint) "
+                        "at --size with tau = --tau-rel x h")
+    p.add_argument("--tau-rel", type=float, default=0.05)
     p.add_argument("--adam-steps", type=int, default=200)
     p.add_argument("--grids", type=int, default=256)
     return p.parse_args()
@@ -663,6 +665,67 @@ def run_adam(args):
     print(json.dumps(line), flush=True)
 
 
+def run_softmin(args):
+    """Forward + record + adjoint of the soft-min relaxation on the n x n
+    inverse-problem workload, tau = tau_rel x h; CUDA events per phase, L2
+    flushed between steps."""
+    import torch
+
+    import rf_inputs as R
+    from paper_2603_00035_gb300 import api
+    from paper_2603_00035_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(0)
+    n = args.size
+    c = R.config_inverse(n=n, seed=0)
+    tau = args.tau_rel * c["h"]
+    raw = torch.from_numpy(c["raw"]).cuda()
+    src = torch.from_numpy(c["src"]).cuda()
+    g = torch.from_numpy(c["g"]).cuda()
+    ctx = api.Context.get(0)
+    proj, _ = api.rf_project(raw, c["eps"], c["delta"])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(timed):
+        if timed:
+            ev[0].record()
+        T = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau)
+        if timed:
+            ev[1].record()
+        wnb, dT = api.rf_softmin_record(proj, c["eps"], src, c["h"], T, tau)
+        if timed:
+            ev[2].record()
+        api.rf_softmin_adjoint(src, T, wnb, dT, g, lam=False)
+        if timed:
+            ev[3].record()
+
+    for _ in range(args.warmup):
+        step(False)
+    st = ctx.stats()
+    if st["status"] != 0:
+        raise RuntimeError(f"soft-min status {st}")
+    iters, adj = st["sweeps"], st["adj_sweeps"]
+    ph = np.zeros(3)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        step(True)
+        torch.cuda.synchronize()
+        ph += np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(3)])
+    ph /= args.steps
+    ms = float(ph.sum())
+    line = {"metric": f"soft-min forward+adjoint solves/s at {n}x{n}", "value": 1e3 / ms, "unit": "solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"soft-min relaxation, {n}x{n} inverse-problem fields, tau = {args.tau_rel} h",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "phase_ms": {"forward": ph[0], "record": ph[1], "adjoint": ph[2]},
+            "jacobi_iterations": iters, "adjoint_iterations": adj, "gpu_launches": 6 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -673,6 +736,8 @@ def main():
         run_appb(args)
     elif args.workload == "adam2048":
         run_adam(args)
+    elif args.workload == "softmin":
+        run_softmin(args)
     else:
         run_ours(args)
 

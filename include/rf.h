@@ -345,6 +345,42 @@ rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src,
                      const float *T, const rf_record *rec, const float *dLdT,
                      float *dLdproj5, float *lambda, int algo, void *stream);
 
+/* ---- soft-min relaxation of the stencil selection --------------------------
+ * Paper: Sec. 3.3 "Stencil Boundaries and Non-Smoothness" names soft-min
+ * relaxations as an alternative to the hard minimum, without a formula.
+ * Reading implemented: each of a node's 8 stencils k (donors k, k+1) has
+ * the value c_k of its segment minimum -- the two-point candidate when valid
+ * (App. A), else the smaller one-point candidate of its finite endpoints --
+ * and the node takes T = -tau log sum_k exp(-c_k / tau) (tau > 0; tau = 0 is
+ * the hard minimum).  T is continuous where a two-point update turns valid,
+ * smooth elsewhere except where validity (causality) switches.  A soft value
+ * lies up to tau log 8 below its candidate minimum: tau must stay well below
+ * the cheapest edge cost (|m|_M - w.m over the grid's steps), else the
+ * values run to -inf -- reported as RF_ERR_NOT_CONVERGED as soon as a
+ * non-source node goes negative.
+ *
+ * rf_softmin_forward: Jacobi iterations of the relaxed system (all nodes,
+ * one persistent launch) from T = 0 on sources, +inf elsewhere (warm mode:
+ * the caller's T), until an iteration changes no node by more than tol +
+ * rtol |T| (opts as rf_sweep_forward; at most max_sweeps x max(ny, nx)
+ * iterations; the iteration count is reported as the sweeps statistic).
+ * Arguments as rf_sweep_forward without the record. */
+rf_status rf_softmin_forward(rf_ctx *ctx, const rf_grid *grid, const float *proj5, float eps,
+                             const uint8_t *src, float tau, const rf_opts *opts, float *T, void *stream);
+/* Record of the relaxed system at T: wnb (8 planes, [8][ny*nx]) =
+ * dT_p / dT(neighbour n of p), dT (5 planes) = dT_p / d(L11, L21, L22, wx,
+ * wy); both zero at sources and unreached nodes.  The weights of a node sum
+ * to 1. */
+rf_status rf_softmin_record(rf_ctx *ctx, const rf_grid *grid, const float *proj5, float eps,
+                            const uint8_t *src, const float *T, float tau, float *wnb, float *dT, void *stream);
+/* Adjoint of the relaxed system: lambda_p = g_p + sum over neighbours q of
+ * wnb_q(q -> p) lambda_q (iterated until no multiplier changes by more than
+ * 1e-7 relative: exact when the weights form a DAG), dLdproj5 = lambda dT
+ * (5 planes, zero at sources and unreached nodes); lambda (nullable). */
+rf_status rf_softmin_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, const float *T,
+                             const float *wnb, const float *dT, const float *dLdT, float *dLdproj5,
+                             float *lambda, void *stream);
+
 /* ---- a10: batched solve ---------------------------------------------------
  * Many grids of uneven size and source count, forward + record (+ adjoint
  * and parameter gradients when dLdT != NULL) in one call.

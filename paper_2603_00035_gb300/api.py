@@ -275,6 +275,48 @@ def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=Non
     return dLdproj5, lam_t
 
 
+# ---- soft-min relaxation (Sec. 3.3) -----------------------------------------------
+
+def rf_softmin_forward(proj5, eps, src, h, tau, opts=None, T=None, ctx=None, stream=None):
+    """Relaxed forward solve: T = softmin_tau over the 8 stencil values."""
+    _check_cuda(proj5, torch.float32, name="proj5")
+    _, ny, nx = proj5.shape
+    _check_cuda(src, torch.uint8, (ny, nx), name="src")
+    ctx = ctx or Context.get(proj5.device)
+    T = T if T is not None else torch.empty((ny, nx), dtype=torch.float32, device=proj5.device)
+    o = opts if opts is not None else make_opts()
+    g = _grid(ny, nx, h)
+    L.check(L.load().rf_softmin_forward(ctx.handle, ctypes.byref(g), _ptr(proj5), float(eps), _ptr(src), float(tau),
+                                        ctypes.byref(o), _ptr(T), _stream(stream)), "rf_softmin_forward")
+    return T
+
+
+def rf_softmin_record(proj5, eps, src, h, T, tau, ctx=None, stream=None):
+    """(wnb (8, ny, nx), dT (5, ny, nx)) of the relaxed system at T."""
+    _, ny, nx = proj5.shape
+    ctx = ctx or Context.get(proj5.device)
+    wnb = torch.empty((8, ny, nx), dtype=torch.float32, device=proj5.device)
+    dT = torch.empty((5, ny, nx), dtype=torch.float32, device=proj5.device)
+    g = _grid(ny, nx, h)
+    L.check(L.load().rf_softmin_record(ctx.handle, ctypes.byref(g), _ptr(proj5), float(eps), _ptr(src), _ptr(T),
+                                       float(tau), _ptr(wnb), _ptr(dT), _stream(stream)), "rf_softmin_record")
+    return wnb, dT
+
+
+def rf_softmin_adjoint(src, T, wnb, dT, dLdT, lam=True, dLdproj5=None, ctx=None, stream=None):
+    """(dL/d(L11, L21, L22, wx, wy), lambda or None) of the relaxed system."""
+    ny, nx = T.shape
+    _check_cuda(dLdT, torch.float32, (ny, nx), name="dLdT")
+    ctx = ctx or Context.get(T.device)
+    dLdproj5 = dLdproj5 if dLdproj5 is not None else torch.empty((5, ny, nx), dtype=torch.float32, device=T.device)
+    lam_t = torch.empty((ny, nx), dtype=torch.float32, device=T.device) if lam else None
+    g = _grid(ny, nx, 1.0)
+    L.check(L.load().rf_softmin_adjoint(ctx.handle, ctypes.byref(g), _ptr(src), _ptr(T), _ptr(wnb), _ptr(dT),
+                                        _ptr(dLdT), _ptr(dLdproj5), _ptr(lam_t), _stream(stream)),
+            "rf_softmin_adjoint")
+    return dLdproj5, lam_t
+
+
 # ---- a10: batched solve ------------------------------------------------------
 
 BATCH_DESC_DTYPE = None  # numpy structured dtype matching rf_batch_desc

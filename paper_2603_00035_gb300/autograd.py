@@ -58,6 +58,34 @@ def rf_solve(raw5, src, h, eps=1e-6, delta=0.05, algo="ordered", opts=None):
     return RFSolve.apply(raw5, src, h, eps, delta, algo, opts)
 
 
+class SoftSolve(torch.autograd.Function):
+    """T = SoftSolve.apply(raw5, src, h, tau, eps, delta, opts): the
+    soft-min relaxation of the solver (Sec. 3.3; each node takes -tau log
+    sum_k exp(-c_k / tau) over its 8 stencil segment minima), differentiated
+    through its own record and adjoint.  Device errors raise RFError."""
+
+    @staticmethod
+    def forward(ctx, raw5, src, h, tau, eps=1e-6, delta=0.05, opts=None):
+        raw5 = raw5.contiguous()
+        proj, clip = api.rf_project(raw5, eps, delta)
+        T = api.rf_softmin_forward(proj, eps, src, h, tau, opts=opts)
+        wnb, dT = api.rf_softmin_record(proj, eps, src, h, T, tau)
+        api.Context.get(raw5.device).raise_on_device_error("SoftSolve.forward")
+        ctx.save_for_backward(raw5, clip, src, T, wnb, dT)
+        ctx.cfg = (eps, delta)
+        return T
+
+    @staticmethod
+    def backward(ctx, gT):
+        raw5, clip, src, T, wnb, dT = ctx.saved_tensors
+        eps, delta = ctx.cfg
+        g = torch.nan_to_num(gT.contiguous().to(torch.float32), nan=0.0, posinf=0.0, neginf=0.0)
+        gproj, _ = api.rf_softmin_adjoint(src, T, wnb, dT, g, lam=False)
+        graw = api.rf_project_backward(raw5, clip, eps, delta, gproj)
+        api.Context.get(raw5.device).raise_on_device_error("SoftSolve.backward")
+        return graw, None, None, None, None, None, None
+
+
 # ---- the paper's own parameterisation (App. B) ---------------------------------
 
 class MetricProject(torch.autograd.Function):

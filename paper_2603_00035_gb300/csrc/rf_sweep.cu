@@ -415,6 +415,10 @@ void init_state(float *T, const uint8_t *src, long long n, int warm, DevState *s
   init_kernel<<<blocks_for(n, 256, num_sms * 8), 256, 0, s>>>(T, src, n, warm, st, has_src);
 }
 
+void check_source_flag(const int *has_src, DevState *st, cudaStream_t s) {
+  check_source_kernel<<<1, 32, 0, s>>>(has_src, st);
+}
+
 struct RecordArgs {
   int ny, nx;
   float h, eps;

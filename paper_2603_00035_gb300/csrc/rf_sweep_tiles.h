@@ -60,6 +60,8 @@ struct TileLaunch {
 // (cold) or the caller's guess (warm); *has_src |= 1 when a source exists.
 void init_state(float *T, const uint8_t *src, long long n, int warm, DevState *st, int *has_src, int num_sms,
                 cudaStream_t s);
+// RF_ERR_NO_SOURCE in the status word when *has_src is 0 (after init_state).
+void check_source_flag(const int *has_src, DevState *st, cudaStream_t s);
 
 // Tile side used for a requested one (0 or < 32: 16; >= 32: 32).
 int tile_side(int requested);
