@@ -102,6 +102,9 @@ def load(path: str = LIB_PATH):
         "rf_tv": [P, ctypes.POINTER(Grid), P, I, F, F, P, P, P],
         "rf_encoder_combine": [P, P, I, I, I, I, P, I, F, P, P],
         "rf_encoder_combine_backward": [P, P, I, I, I, I, I, F, P, P, P],
+        "rf_softmin_forward": [P, ctypes.POINTER(Grid), P, F, P, F, ctypes.POINTER(Opts), P, P],
+        "rf_softmin_record": [P, ctypes.POINTER(Grid), P, F, P, P, F, P, P, P],
+        "rf_softmin_adjoint": [P, ctypes.POINTER(Grid), P, P, P, P, P, P, P, P],
     }
     I64 = ctypes.c_int64
     sig.update({

@@ -40,3 +40,13 @@ def test_host_side_argument_checks(lib):
     assert lib.rf_adjoint(None, ctypes.byref(g), None, None, None, None, None, None, 0, None) == \
         L.RF_ERR_INVALID_ARG
     assert lib.rf_ctx_destroy(None) == L.RF_ERR_INVALID_ARG
+
+
+def test_every_declared_function_has_a_signature():
+    """Each function of include/rf.h gets explicit ctypes argument types (a
+    float passed without them would not convert)."""
+    import inspect
+    from paper_2603_00035_gb300 import _lib as L
+    src = inspect.getsource(L.load)
+    missing = [f for f in L.header_functions() if f != "rf_status_string" and f'"{f}"' not in src]
+    assert not missing, missing
