@@ -60,8 +60,11 @@ enum rf_mode {
 };
 
 enum rf_adjoint_algo {
-  RF_ADJ_SWEEP = 0, /* transposed line sweeps until lambda stops changing   */
-  RF_ADJ_ORDERED = 1 /* radix sort on T, then dependency-ordered gather     */
+  RF_ADJ_SWEEP = 0,   /* transposed line sweeps until lambda stops changing */
+  RF_ADJ_ORDERED = 1, /* radix sort on T, then dependency-ordered gather   */
+  RF_ADJ_LEVELS = 2   /* DAG-depth pass, radix sort on the level, then one
+                         gather per level with a grid barrier between
+                         levels; lambda equals RF_ADJ_ORDERED's bit for bit */
 };
 
 /* Forward-solve kernel variants.  The first three run the paper's schedule
@@ -131,7 +134,8 @@ typedef struct rf_stats {
   int32_t sweeps;       /* directional sweeps run (forward; TILES: node
                            updates / nodes, rounded up)                   */
   int32_t converged;    /* 1 if the last sweep changed nothing            */
-  int32_t adj_sweeps;   /* sweeps of the last adjoint (RF_ADJ_SWEEP)      */
+  int32_t adj_sweeps;   /* sweeps of the last adjoint (RF_ADJ_SWEEP), DAG
+                           levels of the last RF_ADJ_LEVELS adjoint       */
   int64_t cell_updates; /* node updates of the last forward (line sweeps:
                            sweeps * ny * nx; TILES: nodes evaluated)      */
   float max_residual;   /* max |T - min valid candidate(T)| (record pass) */
@@ -340,7 +344,11 @@ rf_status rf_residual(rf_ctx *ctx, const rf_grid *grid, const float *proj5,
  * of J^T lambda = g -- then writes dL/dtheta_p = lambda_p dT0_p/dtheta_p
  * into dLdproj5 (5 planes, zero at sources and unreached nodes).
  * T, rec: from rf_sweep_forward; dLdT: [ny*nx] (ignored where T = +inf);
- * lambda (nullable): [ny*nx] output.  algo: enum rf_adjoint_algo. */
+ * lambda (nullable): [ny*nx] output.  algo: enum rf_adjoint_algo.
+ * RF_ADJ_ORDERED and RF_ADJ_LEVELS wait (bounded by the context's timeout)
+ * for donors or children named by the record; a record whose donors do not
+ * have strictly smaller T ends in RF_ERR_TIMEOUT in the stats, with the
+ * outputs incomplete.  Scratch: the context's buffers, grown as needed. */
 rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src,
                      const float *T, const rf_record *rec, const float *dLdT,
                      float *dLdproj5, float *lambda, int algo, void *stream);

@@ -259,15 +259,15 @@ def rf_residual(proj5, eps, src, h, T, per_node=False, ctx=None, stream=None):
 
 def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=None, stream=None):
     """a6-a8: solve J^T lambda = g on the recorded stencils and contract with
-    the partials.  Returns (dL/d(L11, L21, L22, wx, wy) of the projected
-    fields, lambda or None)."""
+    the partials.  algo: "sweep", "ordered" or "levels".  Returns (dL/d(L11,
+    L21, L22, wx, wy) of the projected fields, lambda or None)."""
     ny, nx = T.shape
     _check_cuda(dLdT, torch.float32, (ny, nx), name="dLdT")
     ctx = ctx or Context.get(T.device)
     dLdproj5 = dLdproj5 if dLdproj5 is not None else torch.empty((5, ny, nx), dtype=torch.float32,
                                                                  device=T.device)
     lam_t = torch.empty((ny, nx), dtype=torch.float32, device=T.device) if lam else None
-    a = {"sweep": L.RF_ADJ_SWEEP, "ordered": L.RF_ADJ_ORDERED}[algo]
+    a = {"sweep": L.RF_ADJ_SWEEP, "ordered": L.RF_ADJ_ORDERED, "levels": L.RF_ADJ_LEVELS}[algo]
     g = _grid(ny, nx, 1.0)
     crec = rec.c()
     L.check(L.load().rf_adjoint(ctx.handle, ctypes.byref(g), _ptr(src), _ptr(T), ctypes.byref(crec),

@@ -406,6 +406,241 @@ __global__ void ordered_unreached_kernel(const float *T, float *grad, float *lam
   }
 }
 
+
+// ---- RF_ADJ_LEVELS: a DAG-depth pass, then a level-synchronous gather ----
+//
+// The record's donor edges form a DAG (a donor's T is strictly below its
+// child's).  The depth pass gives every reached node its level, the length
+// of the longest donor chain from a node without donors (sources: level 0),
+//     level_q = 1 + max over donors p of q of level_p,
+// by walking the T order upwards with the same ticketed, dependency-polling
+// scheme as the ordered gather (a node waits for at most two donors).  A
+// child's level exceeds each of its donors' levels, so after a radix sort on
+// the level the gather processes whole levels from the deepest to level 0,
+// one grid-wide barrier between levels, with plain loads of the children's
+// multipliers: no per-node polling.  The multiplier of each node is the same
+// fixed-order sum as in the ordered gather, so the two agree bit for bit.
+
+struct LevelArgs {
+  int ny, nx;
+  long long n;
+  const uint8_t *src;
+  const float *T;
+  const uint8_t *id;
+  const float *w1;
+  const float *dT;
+  const float *g;
+  const unsigned *order;      // depth pass: node indices by decreasing T
+  unsigned long long *state;  // depth pass: (epoch << 32) | level
+  unsigned epoch;
+  unsigned *ticket;
+  unsigned *level;            // depth pass output: level of each node (n for unreached nodes)
+  unsigned *n_levels;         // depth pass: 1 + the largest level (0: no reached node)
+  const unsigned *by_level;   // gather: node indices sorted by level
+  const unsigned *start;      // gather: first position of each level in by_level
+  unsigned long long *bar;    // gather: arrivals at the level barrier (monotone)
+  float *lam;                 // gather: multipliers (internal)
+  float *grad;
+  float *lam_out;
+  LaunchCtl ctl;
+};
+
+__device__ __forceinline__ bool in_grid(int i, int j, int ny, int nx) {
+  return i >= 0 && i < ny && j >= 0 && j < nx;
+}
+
+__global__ void __launch_bounds__(256) level_depth_kernel(LevelArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long n = a.n;
+  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  unsigned wmax = 0;
+  while (true) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(a.ticket, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= n || ld_acquire_s32(a.ctl.abort)) break;
+    const long long pos = (long long)base + lane;
+    bool done = pos >= n;
+    long long q = -1;
+    int qi = 0, qj = 0, d0 = -1, d1 = -1;
+    if (!done) {
+      q = a.order[n - 1 - pos];  // increasing T
+      if (!(a.T[q] < kInf)) {
+        a.level[q] = (unsigned)n;  // unreached: sorted past every level
+        done = true;
+      } else {
+        qi = (int)(q / a.nx);
+        qj = (int)(q - (long long)qi * a.nx);
+        const uint8_t idq = a.id[q];
+        if (idq & 0x30) d0 = idq & 7;
+        if (idq & 0x20) d1 = (d0 + 1) & 7;
+        // a record names in-grid donors only; drop any other
+        if (d0 >= 0 && !in_grid(qi + nb_dy(d0), qj + nb_dx(d0), a.ny, a.nx)) d0 = -1;
+        if (d1 >= 0 && !in_grid(qi + nb_dy(d1), qj + nb_dx(d1), a.ny, a.nx)) d1 = -1;
+      }
+    }
+    const unsigned long long t0 = gtimer();
+    unsigned spins = 0;
+    while (!__all_sync(0xffffffffu, done)) {
+      if (!done) {
+        bool ready = true;
+        unsigned lv = 0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int d = u ? d1 : d0;
+          if (d >= 0) {
+            const long long pn = (long long)(qi + nb_dy(d)) * a.nx + (qj + nb_dx(d));
+            const unsigned long long v = ld_relaxed_u64(&a.state[pn]);
+            ready = ready && ((v & 0xffffffff00000000ull) == tag);
+            lv = max(lv, (unsigned)v + 1u);
+          }
+        }
+        if (ready) {
+          st_relaxed_u64(&a.state[q], tag | lv);
+          a.level[q] = lv;
+          wmax = max(wmax, lv + 1u);
+          done = true;
+        } else if ((++spins & 63) == 0 &&
+                   ((long long)(gtimer() - t0) > a.ctl.timeout_ns || ld_acquire_s32(a.ctl.abort))) {
+          raise_timeout(a.ctl);
+          done = true;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if (lane == 0 && wmax) atomicMax(a.n_levels, wmax);
+}
+
+// start[l] = first position of level l in the level-sorted keys, for every
+// level present; start[l + 1] = one past its last.  Levels run 0..max
+// without gaps (a node of level l > 0 has a donor of level l - 1).
+__global__ void level_starts_kernel(const unsigned *keys, unsigned *start, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned k = keys[i];
+    if (k >= (unsigned)n) continue;
+    if (i == 0 || keys[i - 1] != k) start[k] = (unsigned)i;
+    if (i == n - 1 || keys[i + 1] != k) start[k + 1] = (unsigned)(i + 1);
+  }
+}
+
+// Bounded barrier on a monotone arrival counter, in two halves so that a
+// CTA can fetch the next level's static data between them: the k-th
+// barrier of the launch waits for k * gridDim.x arrivals (no reset, one
+// atomic per CTA).
+__device__ __forceinline__ void level_arrive(unsigned long long *bar) {
+  __syncthreads();
+  // release: the CTA's stores before the __syncthreads become visible to
+  // every CTA that acquires the counter past this arrival
+  if (threadIdx.x == 0)
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(bar), "l"(1ull) : "memory");
+}
+
+__device__ __forceinline__ bool level_wait(unsigned long long *bar, unsigned long long target, const LaunchCtl &c) {
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_acquire_u64(bar) < target) {
+      const unsigned long long t0 = gtimer();
+      while (ld_acquire_u64(bar) < target) {
+        if ((long long)(gtimer() - t0) > c.timeout_ns || ld_acquire_s32(c.abort)) {
+          raise_timeout(c);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// What a node of the level gather needs besides its children's multipliers:
+// fetched before the barrier that precedes its level, so that after the
+// barrier only the multipliers remain to be loaded.
+struct LevelNode {
+  long long p;    // -1: no node
+  float cw[8];    // child weights in neighbour order (0: not a child)
+  float g;
+  bool act;       // the node has a gradient (recorded update, not a source)
+  float d[5];     // dT0/dtheta
+};
+
+__device__ __forceinline__ void level_fetch(const LevelArgs &a, long long i, long long e, LevelNode &v) {
+  v.p = -1;
+  if (i >= e) return;
+  const long long p = a.by_level[i], n = a.n;
+  const int pi = (int)(p / a.nx), pj = (int)(p - (long long)pi * a.nx);
+  v.p = p;
+  v.g = a.g[p];
+#pragma unroll
+  for (int nb = 0; nb < 8; ++nb) {
+    const int ii = pi + nb_dy(nb), jj = pj + nb_dx(nb);
+    v.cw[nb] = 0.0f;
+    if (ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx) {
+      const long long qn = (long long)ii * a.nx + jj;
+      v.cw[nb] = child_weight(a.id[qn], a.w1[qn], (nb + 4) & 7);
+    }
+  }
+  v.act = a.id[p] != 0 && !a.src[p];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) v.d[c] = a.dT[c * n + p];  // not behind act: one round trip fewer
+}
+
+__device__ __forceinline__ void level_finish(const LevelArgs &a, const LevelNode &v) {
+  if (v.p < 0) return;
+  const long long p = v.p, n = a.n;
+  const int pi = (int)(p / a.nx), pj = (int)(p - (long long)pi * a.nx);
+  float acc = v.g;
+#pragma unroll
+  for (int nb = 0; nb < 8; ++nb)
+    if (v.cw[nb] != 0.0f)
+      acc = fmaf(v.cw[nb], __ldcg(a.lam + (long long)(pi + nb_dy(nb)) * a.nx + (pj + nb_dx(nb))), acc);
+  __stcg(a.lam + p, acc);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) a.grad[c * n + p] = v.act ? acc * v.d[c] : 0.0f;
+  if (a.lam_out) a.lam_out[p] = acc;
+}
+
+// Level starts held in shared memory for the first kLevelSmem levels.
+constexpr int kLevelSmem = 16384;
+
+__global__ void __launch_bounds__(512) level_gather_kernel(LevelArgs a) {
+  extern __shared__ unsigned s_start[];
+  const long long n = a.n;
+  // levels 0 .. nl - 1, counted by the depth pass; none if it gave up
+  const long long nl = ld_acquire_s32(a.ctl.abort) ? 0 : min((long long)*a.n_levels, n);
+  const long long held = min(nl + 1, (long long)kLevelSmem);
+  for (long long k = threadIdx.x; k < held; k += blockDim.x) s_start[k] = a.start[k];
+  __syncthreads();
+  auto level_start = [&](long long L) -> long long {
+    return min((long long)(L < held ? s_start[L] : a.start[L]), n);
+  };
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+  unsigned long long step = 0;
+  LevelNode v;
+  v.p = -1;
+  if (nl > 0) level_fetch(a, level_start(nl - 1) + gt, level_start(nl), v);
+  for (long long L = nl - 1; L >= 0; --L) {
+    level_finish(a, v);
+    // a level wider than the grid of threads: the rest without prefetch
+    const long long e = level_start(L + 1);
+    for (long long i = level_start(L) + gt + gs; i < e; i += gs) {
+      LevelNode w;
+      level_fetch(a, i, e, w);
+      level_finish(a, w);
+    }
+    if (L == 0) break;
+    level_arrive(a.bar);
+    level_fetch(a, level_start(L - 1) + gt, level_start(L), v);  // overlaps the barrier
+    if (!level_wait(a.bar, (++step) * gridDim.x, a.ctl)) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl.st->adj_sweeps = (int)nl;
+}
+
 }  // namespace rf
 
 using namespace rf;
@@ -413,6 +648,21 @@ using namespace rf;
 namespace {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Next launch epoch for the tagged per-node state words (cleared on first
+// use and whenever the epoch counter wraps).
+rf_status next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, unsigned *epoch) {
+  const bool fresh = ctx->adj_state_cap < (size_t)n || !ctx->adj_state;
+  rf_status rs;
+  if ((rs = ensure(&ctx->adj_state, &ctx->adj_state_cap, (size_t)n)) != RF_OK) return rs;
+  if (fresh || ctx->adj_epoch == 0xffffffffu) {
+    if (cudaMemsetAsync(ctx->adj_state, 0, sizeof(unsigned long long) * ctx->adj_state_cap, s) != cudaSuccess)
+      return RF_ERR_CUDA;
+    ctx->adj_epoch = 0;
+  }
+  *epoch = ++ctx->adj_epoch;
+  return RF_OK;
+}
 
 }  // namespace
 
@@ -439,16 +689,8 @@ rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid 
            *vout = (unsigned *)(base + 3 * arr);
   unsigned *ctl_words = (unsigned *)(base + 4 * arr);  // [0] ticket, [1] abort
   void *temp = base + 4 * arr + 256;
-  // per-node state words tagged with a launch epoch (cleared on first use
-  // and whenever the epoch counter wraps)
-  const bool fresh = ctx->adj_state_cap < (size_t)n || !ctx->adj_state;
-  if ((rs = ensure(&ctx->adj_state, &ctx->adj_state_cap, (size_t)n)) != RF_OK) return rs;
-  if (fresh || ctx->adj_epoch == 0xffffffffu) {
-    if (cudaMemsetAsync(ctx->adj_state, 0, sizeof(unsigned long long) * ctx->adj_state_cap, s) != cudaSuccess)
-      return RF_ERR_CUDA;
-    ctx->adj_epoch = 0;
-  }
-  const unsigned epoch = ++ctx->adj_epoch;
+  unsigned epoch;
+  if ((rs = next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
   if (cudaMemsetAsync(ctl_words, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return RF_ERR_CUDA;
 
   ordered_keys_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, kin, vin, n);
@@ -494,6 +736,93 @@ rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid 
   return cuda_status(cudaGetLastError());
 }
 
+
+// The level-scheduled adjoint of one grid: T order (radix sort), the depth
+// pass, a radix sort on the level, the level starts, the level gather.
+rf_status adjoint_levels(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const float *T, const rf_record *rec,
+                         const float *dLdT, float *dLdproj5, float *lambda, cudaStream_t s) {
+  ctx->last_stream = s;
+  const long long n = (long long)ny * nx;
+  int lbits = 1;  // level keys are <= n
+  while (lbits < 32 && ((unsigned long long)n >> lbits) != 0) ++lbits;
+  size_t t1 = 0, t2 = 0;
+  if (cub::DeviceRadixSort::SortPairs(nullptr, t1, (unsigned *)nullptr, (unsigned *)nullptr, (unsigned *)nullptr,
+                                      (unsigned *)nullptr, (int)n, 0, 32, s) != cudaSuccess ||
+      cub::DeviceRadixSort::SortPairs(nullptr, t2, (unsigned *)nullptr, (unsigned *)nullptr, (unsigned *)nullptr,
+                                      (unsigned *)nullptr, (int)n, 0, lbits, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+  size_t temp_bytes = std::max(t1, t2);
+  const size_t arr = align_up((size_t)n * sizeof(unsigned)), arr1 = align_up((size_t)(n + 1) * sizeof(unsigned));
+  const size_t need = 4 * arr + arr1 + 256 + align_up(temp_bytes);
+  rf_status rs;
+  if ((rs = ensure((unsigned char **)&ctx->scratch, &ctx->scratch_cap, need)) != RF_OK) return rs;
+  unsigned char *base = (unsigned char *)ctx->scratch;
+  unsigned *kin = (unsigned *)base, *kout = (unsigned *)(base + arr), *vin = (unsigned *)(base + 2 * arr),
+           *vout = (unsigned *)(base + 3 * arr), *start = (unsigned *)(base + 4 * arr);
+  // control words: [0] ticket, [1] abort, [2] level count, [4..5] barrier counter
+  unsigned *ctl_words = (unsigned *)(base + 4 * arr + arr1);
+  void *temp = base + 4 * arr + arr1 + 256;
+  if ((rs = ensure(&ctx->lbuf, &ctx->lbuf_cap, (size_t)n)) != RF_OK) return rs;
+  unsigned epoch;
+  if ((rs = next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
+  if (cudaMemsetAsync(ctl_words, 0, 6 * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(&ctx->state->adj_sweeps, 0, sizeof(int), s) != cudaSuccess)
+    return RF_ERR_CUDA;
+
+  ordered_keys_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, kin, vin, n);
+  if (cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, (int)n, 0, 32, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+
+  LevelArgs a;
+  a.ny = ny;
+  a.nx = nx;
+  a.n = n;
+  a.src = src;
+  a.T = T;
+  a.id = rec->id;
+  a.w1 = rec->w1;
+  a.dT = rec->dT;
+  a.g = dLdT;
+  a.order = vout;
+  a.state = ctx->adj_state;
+  a.epoch = epoch;
+  a.ticket = ctl_words;
+  a.level = kin;  // the T keys are consumed
+  a.n_levels = ctl_words + 2;
+  a.by_level = vout;  // the T order is consumed by the depth pass
+  a.start = start;
+  a.bar = (unsigned long long *)(ctl_words + 4);
+  a.lam = ctx->lbuf;
+  a.grad = dLdproj5;
+  a.lam_out = lambda;
+  a.ctl.st = ctx->state;
+  a.ctl.abort = (int *)(ctl_words + 1);
+  a.ctl.timeout_ns = ctx->timeout_ns;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_depth_kernel, 256, 0) != cudaSuccess ||
+      per_sm < 1)
+    return RF_ERR_CUDA;
+  // every warp that takes a ticket must be resident: cooperative launch
+  void *args[] = {&a};
+  if (cudaLaunchCooperativeKernel((const void *)level_depth_kernel, dim3(per_sm * ctx->num_sms), dim3(256), args,
+                                  0, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+  // group the nodes by level (vin still holds 0..n-1: the sort leaves its inputs)
+  if (cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, (int)n, 0, lbits, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+  level_starts_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(kout, start, n);
+  // one CTA of 512 threads per SM: the widest level of a 2048^2 grid (a few
+  // thousand nodes) fits in one pass, and the barrier takes one arrival per SM
+  const size_t gsmem = kLevelSmem * sizeof(unsigned);
+  if (cudaFuncSetAttribute(level_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem) !=
+          cudaSuccess ||
+      cudaLaunchCooperativeKernel((const void *)level_gather_kernel, dim3(ctx->num_sms), dim3(512), args, gsmem,
+                                  s) != cudaSuccess)
+    return RF_ERR_CUDA;
+  ordered_unreached_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, dLdproj5, lambda, n);
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace rf
 
 extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, const float *T,
@@ -502,8 +831,10 @@ extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t 
   if (!ctx || !grid_ok(grid) || !src || !T || !rec || !rec->id || !rec->w1 || !rec->dT || !dLdT ||
       !dLdproj5)
     return RF_ERR_INVALID_ARG;
-  if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED) return RF_ERR_INVALID_ARG;
+  if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED && algo != RF_ADJ_LEVELS) return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  if (algo == RF_ADJ_LEVELS)
+    return rf::adjoint_levels(ctx, grid->ny, grid->nx, src, T, rec, dLdT, dLdproj5, lambda, (cudaStream_t)stream);
   if (algo == RF_ADJ_ORDERED)
     return rf::adjoint_ordered(ctx, grid->ny, grid->nx, (long long)grid->ny * grid->nx, nullptr, 1, src, T, rec,
                                dLdT, dLdproj5, lambda, (cudaStream_t)stream);
@@ -541,7 +872,7 @@ extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t 
   if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)max_sweeps + 2)) != RF_OK) return rs;
   cudaMemsetAsync(ctx->progress, 0, sizeof(unsigned) * (grid_ + 1), s);
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (max_sweeps + 2), s);
-  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 2, s);
+  cudaMemsetAsync(&ctx->state->bar, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(&ctx->state->adj_sweeps, 0, sizeof(int), s);
   cudaMemsetAsync(ctx->lbuf, 0, sizeof(float) * n, s);  // lambda starts at 0
 

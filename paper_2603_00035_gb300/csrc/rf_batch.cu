@@ -406,7 +406,7 @@ rf_status batch_tiles(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids, int6
   if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2)) != RF_OK) return rs;
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
   cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
-  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 4, s);
+  cudaMemsetAsync(&ctx->state->bar, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned), s);
   cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
   int *has_src = ctx->changed + o.max_sweeps;  // per-grid sources are checked by the seed kernel
   rf::init_state(T, src, total_nodes, o.mode == RF_MODE_WARM, ctx->state, has_src, ctx->num_sms, s);

@@ -232,6 +232,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ int ld_acquire_s32(const int *p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -244,8 +249,7 @@ struct DevState {
   int sweeps;
   int converged;
   int adj_sweeps;
-  unsigned bar_count;  // grid barrier arrivals
-  unsigned bar_gen;    // grid barrier generation
+  unsigned long long bar;  // grid barrier arrivals of the running launch (zeroed before it)
   unsigned max_res_bits;  // float bits of max |residual| (non-negative)
   unsigned rounds;        // rounds of the last tile-queue solve
   unsigned long long cell_updates;

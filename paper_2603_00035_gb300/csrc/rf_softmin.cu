@@ -336,7 +336,7 @@ extern "C" rf_status rf_softmin_forward(rf_ctx *ctx, const rf_grid *grid, const 
   if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)8)) != RF_OK) return rs;
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * 8, s);
   cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
-  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 4, s);
+  cudaMemsetAsync(&ctx->state->bar, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned), s);
   int *has_src = ctx->changed + 4;
   init_state(T, src, n, o.mode == RF_MODE_WARM, ctx->state, has_src, ctx->num_sms, s);
   check_source_flag(has_src, ctx->state, s);
@@ -394,7 +394,7 @@ extern "C" rf_status rf_softmin_adjoint(rf_ctx *ctx, const rf_grid *grid, const 
   if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)8)) != RF_OK) return rs;
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * 8, s);
   cudaMemsetAsync(&ctx->state->adj_sweeps, 0, sizeof(int), s);
-  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 2, s);
+  cudaMemsetAsync(&ctx->state->bar, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(ctx->lbuf, 0, sizeof(float) * n, s);
   SoftAdjArgs a;
   a.ny = ny;

@@ -557,7 +557,7 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
     if (rt == RF_OK) {
       cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
       cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
-      cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 4, s);
+      cudaMemsetAsync(&ctx->state->bar, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned), s);
       cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
       int *has_src = ctx->changed + o.max_sweeps;
       init_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, src, n, o.mode == RF_MODE_WARM,
@@ -641,7 +641,7 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
   cudaMemsetAsync(ctx->progress, 0, sizeof(unsigned) * (grid_ctas + 1), s);
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
   cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
-  cudaMemsetAsync(&ctx->state->bar_count, 0, sizeof(unsigned) * 4, s);
+  cudaMemsetAsync(&ctx->state->bar, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned), s);
   cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
 
   int *has_src = ctx->changed + o.max_sweeps;  // last slot
