@@ -38,9 +38,10 @@ ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-
 # DRAM bytes (read + write) of one launch of the tile-queue forward kernel on the 2048^2 workload (16x16
 # tiles, default window), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).  Reported
 # as roofline.traffic only while the kernel's sources hash to the captured build's.
-TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048): {"sources_sha16": "34a8496fb6f4477c",
-                                                       "bytes": 310743552 + 41989120}}
-TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_00035_gb300/csrc/rf_cone.cuh"]
+TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048): {"sources_sha16": "c0a55d995bf9cc55",
+                                                       "bytes": 313101824 + 42092544}}
+TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_00035_gb300/csrc/rf_cone.cuh",
+                   "paper_2603_00035_gb300/csrc/rf_sweep_common.cuh", "paper_2603_00035_gb300/csrc/rf_device.cuh"]
 # kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
 # source check, then tile queue: plan, reset, seed, finish-seed, solve, stats; streamed: node records +
 # sweep; tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels

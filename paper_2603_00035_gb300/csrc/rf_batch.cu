@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "rf_adjoint.h"
+#include "rf_cone.cuh"
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
 #include "rf_sweep_tiles.h"
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchArgs a) {
       const int i = (int)(p / nx), j = (int)(p - (long long)i * nx);
       uint8_t id;
       float w1, dd[5], r;
-      record_node(fg, a.total, p, i, j, ny, nx, h, a.eps, sg[p] != 0, Tg, true, id, w1, dd, r);
+      record_node_cone(fg, a.total, p, i, j, ny, nx, h, a.eps, sg[p] != 0, Tg, true, id, w1, dd, r);
       a.id[d.offset + p] = id;
       a.w1[d.offset + p] = w1;
 #pragma unroll
@@ -356,7 +357,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(BatchArgs a) {
 }
 
 // a5 for packed grids (blockIdx.y = grid): stencil ids, donor weights and
-// partials of every node at the converged T, and the max residual.
+// partials of every node at the converged T (cone form, as the tile queue
+// that solved them), and the max residual.
 __global__ void __launch_bounds__(256) batch_record_kernel(const TGrid *grids, long long total, const float *f,
                                                            float eps, const uint8_t *src, const float *T,
                                                            uint8_t *id, float *w1, float *dT, DevState *st) {
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(256) batch_record_kernel(const TGrid *grids, l
     const long long p = g.node_off + q;
     uint8_t idv;
     float w1v, d[5], r;
-    record_node(f + g.node_off, total, q, i, j, g.ny, g.nx, g.h, eps, src[p] != 0, T + g.node_off, true, idv,
+    record_node_cone(f + g.node_off, total, q, i, j, g.ny, g.nx, g.h, eps, src[p] != 0, T + g.node_off, true, idv,
                 w1v, d, r);
     id[p] = idv;
     w1[p] = w1v;

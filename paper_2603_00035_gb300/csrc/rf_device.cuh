@@ -157,63 +157,6 @@ __device__ __forceinline__ Winner winner(const float tab[kTabSize], const float 
   return w;
 }
 
-// Stencil record of node (i, j) at the converged T (Alg. 2 first loop;
-// App. A closed-form partials).  f: 5 planes (stride `plane`) of the
-// projected fields; T: the converged times.  For the winning update with
-// barycentric weights (w1, 1 - w1) the characteristic displacement is
-// v = w1 m1 + (1-w1) m2 (v = m_n for a one-point update) and
-//   dT0/dw = -v,  dT0/dM = v v^T / (2 |v|_M),  dT0/dL = 2 (dT0/dM) L.
-// Also returns r = T - min valid candidate(T) (the residual).
-__device__ __forceinline__ void record_node(const float *f, long long plane, long long p, int i, int j, int ny,
-                                            int nx, float h, float eps, bool is_src, const float *T, bool want_rec,
-                                            uint8_t &id, float &w1, float d[5], float &r) {
-  id = 0;
-  w1 = 0.0f;
-  r = 0.0f;
-#pragma unroll
-  for (int c = 0; c < 5; ++c) d[c] = 0.0f;
-  const float T0 = T[p];
-  if (is_src || !(T0 < kInf)) return;
-  float Tn[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int ii = i + nb_dy(q), jj = j + nb_dx(q);
-    Tn[q] = (ii >= 0 && ii < ny && jj >= 0 && jj < nx) ? T[(long long)ii * nx + jj] : kInf;
-  }
-  const float l11 = f[p], l21 = f[plane + p], l22 = f[2 * plane + p], wx = f[3 * plane + p], wy = f[4 * plane + p];
-  float tab[kTabSize];
-  node_tab(l11, l21, l22, wx, wy, h, eps, tab);
-  const Winner wall = winner(tab, Tn);
-  if (wall.value < kInf) r = T0 - wall.value;
-  if (!want_rec) return;
-  // the record names only donors strictly earlier than the node
-  const Winner w = winner(tab, Tn, T0);
-  if (!w.id) return;
-  id = w.id;
-  float vx, vy;
-  const int k = w.id & 7;
-  if (w.id & 0x20) {
-    const float sum = w.l1 + w.l2;
-    w1 = sum > 0.0f ? w.l1 / sum : 0.5f;
-    const int k2 = (k + 1) & 7;
-    vx = h * (w1 * (float)nb_dx(k) + (1.0f - w1) * (float)nb_dx(k2));
-    vy = h * (w1 * (float)nb_dy(k) + (1.0f - w1) * (float)nb_dy(k2));
-  } else {
-    w1 = 1.0f;
-    vx = h * (float)nb_dx(k);
-    vy = h * (float)nb_dy(k);
-  }
-  const float m11 = fmaf(l11, l11, eps), m12 = l11 * l21, m22 = fmaf(l21, l21, fmaf(l22, l22, eps));
-  const float vm = sqrtf(vx * (m11 * vx + m12 * vy) + vy * (m12 * vx + m22 * vy));
-  const float s = 0.5f / vm;
-  const float D11 = s * vx * vx, D12 = s * vx * vy, D22 = s * vy * vy;
-  d[0] = 2.0f * (D11 * l11 + D12 * l21);
-  d[1] = 2.0f * (D12 * l11 + D22 * l21);
-  d[2] = 2.0f * D22 * l22;
-  d[3] = -vx;
-  d[4] = -vy;
-}
-
 // Weight with which child q (record id, w1) passes lambda to the neighbour in
 // direction `back` (the direction from q to that neighbour); 0 if none.
 __device__ __forceinline__ float child_weight(uint8_t id, float w1, int back) {

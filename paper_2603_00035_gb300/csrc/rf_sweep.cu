@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "rf_cone.cuh"
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
 #include "rf_sweep_stream.h"
@@ -434,7 +435,8 @@ struct RecordArgs {
 };
 
 // a5: stencil identification + closed-form partials at the converged T
-// (record_node), with the max |residual| reduced per block.
+// (record_node_cone: the cone form of the tile-queue and streamed solves,
+// one pass over the candidates), with the max |residual| reduced per block.
 template <bool RECORD>
 __global__ void __launch_bounds__(256) record_kernel(RecordArgs a) {
   const long long n = (long long)a.ny * a.nx;
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(256) record_kernel(RecordArgs a) {
     const int i = (int)(p / a.nx), j = (int)(p - (long long)i * a.nx);
     uint8_t id;
     float w1, d[5], r;
-    record_node(a.f, n, p, i, j, a.ny, a.nx, a.h, a.eps, a.src[p] != 0, a.T, RECORD, id, w1, d, r);
+    record_node_cone(a.f, n, p, i, j, a.ny, a.nx, a.h, a.eps, a.src[p] != 0, a.T, RECORD, id, w1, d, r);
     if (RECORD) {
       a.id[p] = id;
       a.w1[p] = w1;
