@@ -227,9 +227,14 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
     if (r > a.max_rounds) break;
     const float theta = cert ? kInf : __uint_as_float(__ldcg(&cur->kmin)) + a.window;
 
+    // the first list entry of every group is its own (no atomic at the start
+    // of a round, where all groups would contend for one counter); later
+    // entries are handed out by the counter
+    bool first_take = true;
     while (true) {
       if (gt == 0) {
-        const unsigned k = atomicAdd(&cur->grab, 1u);
+        const unsigned ngroups = gridDim.x * G::GROUPS;
+        const unsigned k = first_take ? blockIdx.x * G::GROUPS + grp : ngroups + atomicAdd(&cur->grab, 1u);
         S.go = k < n;
         int t = -1;
         if (k < n && cert) {
@@ -250,6 +255,7 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
         }
       }
       group_sync<NG>(bar);
+      first_take = false;
       if (!S.go) break;
       const int t = S.tile;
       const unsigned kb = S.key;
@@ -282,12 +288,25 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
       int hr = 0, hc = 0, gi = -1, gj = -1;
       float prev = kInf;
       float *hp = nullptr;
+      // T of the node and of its halo node from both buffers, before the
+      // parities are known: the round-start buffer of a tile is not written
+      // during the round, so the one selected below is current
+      float tb0 = kInf, tb1 = kInf, hv0 = kInf, hv1 = kInf;
+      if (inb) {
+        tb0 = __ldcg(a.T[0] + p);
+        tb1 = __ldcg(a.T[1] + p);
+      }
       if (gt < G::HALO) {
         halo_rc<TS>(gt, hr, hc);
         gi = i0 - 1 + hr;
         gj = j0 - 1 + hc;
         hp = w.halo + (size_t)t * G::HALO + gt;
         prev = __ldcg(hp);
+        if (gi >= 0 && gi < gny && gj >= 0 && gj < gnx) {
+          const long long hq = goff + (long long)gi * gnx + gj;
+          hv0 = __ldcg(a.T[0] + hq);
+          hv1 = __ldcg(a.T[1] + hq);
+        }
       }
       // buffer parities of this tile and its eight neighbours as of the
       // round's start (index (di + 1) * 3 + (dj + 1)); the first-visit flag
@@ -316,16 +335,13 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
       group_sync<NG>(bar);
       const int pt = S.par[4];
       float *Tout = a.T[1 - pt];
-      float tcur = inb ? __ldcg(a.T[pt] + p) : kInf;
+      float tcur = pt ? tb1 : tb0;
       // halo ring, from the neighbours' round-start versions; nodes whose
       // value differs from this tile's previous visit seed the change masks
       if (gt < G::HALO) {
-        float v = kInf;
-        if (gi >= 0 && gi < gny && gj >= 0 && gj < gnx) {
-          const int di = (hr == 0) ? -1 : (hr == G::TW - 1) ? 1 : 0;
-          const int dj = (hc == 0) ? -1 : (hc == G::TW - 1) ? 1 : 0;
-          v = __ldcg(a.T[S.par[(di + 1) * 3 + dj + 1]] + goff + (long long)gi * gnx + gj);
-        }
+        const int di = (hr == 0) ? -1 : (hr == G::TW - 1) ? 1 : 0;
+        const int dj = (hc == 0) ? -1 : (hc == G::TW - 1) ? 1 : 0;
+        const float v = S.par[(di + 1) * 3 + dj + 1] ? hv1 : hv0;
         S.Ts[0][hr][hc] = v;
         S.Ts[1][hr][hc] = v;
         if (node_changed(v, prev, a.tol, a.rtol)) atomicOr(&S.rowm[0][hr], frame_bit<TS>(hc));
