@@ -36,10 +36,9 @@ METRIC = "forward+adjoint solves/s at 2048x2048"
 UNIT = "solves/s"
 ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-update
 # DRAM bytes (read + write) of one launch of the tile-queue forward kernel on the 2048^2 workload (16x16
-# tiles, default window), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).  Reported
-# as roofline.traffic only while the kernel's sources hash to the captured build's.
-TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048): {"sources_sha16": "c0a55d995bf9cc55",
-                                                       "bytes": 313101824 + 42092544}}
+# tiles), by delta-stepping window, each from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
+# Reported as roofline.traffic only while the kernel's sources hash to the captured build's.
+TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048, 4.0): {"sources_sha16": "74ca516c7c09024d", "bytes": 429614336 + 46708224}}
 TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_00035_gb300/csrc/rf_cone.cuh",
                    "paper_2603_00035_gb300/csrc/rf_sweep_common.cuh", "paper_2603_00035_gb300/csrc/rf_device.cuh"]
 # kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
@@ -390,9 +389,8 @@ def run_ours(args):
         bytes_per_launch = 60 * n * n
     achieved = bytes_per_launch / (phase_ms[dom] / 1e3) / 1e9
     traffic = None
-    if names[dom] == "sweep_forward" and tile["variant"] in (0, 8) and tile["band"] in (0, 16) and \
-            tile["window"] == 0.0:
-        cap = TRAFFIC_CAPTURES.get(("tile_solve_kernel<16>", n))
+    if names[dom] == "sweep_forward" and tile["variant"] in (0, 8) and tile["band"] in (0, 16):
+        cap = TRAFFIC_CAPTURES.get(("tile_solve_kernel<16>", n, float(tile["window"] or 4.0)))
         if cap and sources_sha16(TRAFFIC_SOURCES) == cap["sources_sha16"]:
             traffic = cap["bytes"]
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",

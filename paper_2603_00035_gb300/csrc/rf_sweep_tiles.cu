@@ -56,20 +56,30 @@ namespace rf {
 
 constexpr int kTileCta = 1024;     // threads per CTA (one or four tile groups)
 constexpr unsigned kInfBits = 0x7f800000u;
-constexpr int kSlots = 3;          // list / counter slots (round mod 3)
+constexpr int kSlots = 8;          // round slots (round mod 8)
+constexpr int kKeySlots = 4;       // queue-key slots (round mod 4)
 
-// control words of one round slot
+// Control words of one round slot (32 bytes).  A slot serves round r, then
+// round r + 8: it is reset for its next round when round r + 4 completes.
 struct TileSlot {
-  unsigned count;  // tiles queued for the round
-  unsigned grab;   // next list entry to hand out
-  unsigned kmin;   // float bits of the smallest queued key
-  unsigned pad;
+  unsigned long long take;  // (round << 32) | list entries handed out past the groups' own first ones
+  unsigned count;           // tiles queued for the round
+  unsigned kmin;            // float bits of the smallest queued key
+  unsigned done;            // entries finished; kPrevDone - (entries) added once the previous round is complete
+  unsigned moved;           // tiles that published a new version in the round
+  unsigned pad0;
+  unsigned round;           // round the slot serves
 };
-// ctrl layout (unsigned words): 3 slots x 4, the tile count, a spare word,
-// tiles that published a new version [3] (by round mod 3)
-constexpr int kCtrlNT = kSlots * 4;      // tiles of all grids (plan kernel)
-constexpr int kCtrlMoved = kCtrlNT + 2;  // [3]
-
+// ctrl layout (unsigned words): 8 slots x 8 words, then the tile count, the
+// last round up to which every round is complete, the stop flag (1
+// converged, 2 round cap) and the rounds of the solve
+constexpr int kCtrlNT = kSlots * 8;
+constexpr int kCtrlComplete = kCtrlNT + 1;
+constexpr int kCtrlStop = kCtrlNT + 2;
+constexpr int kCtrlRounds = kCtrlNT + 3;
+constexpr int kCtrlBytes = 512;
+static_assert(sizeof(TileSlot) == 32, "slot layout");
+static_assert((kCtrlRounds + 1) * 4 <= kCtrlBytes, "ctrl words");
 
 template <int TS>
 struct TileGeom {
@@ -95,7 +105,9 @@ struct alignas(16) GroupSmem {
   float t0[TileGeom<TS>::NODES];  // node values at the start of the visit
   TGrid gd;      // grid of the current tile
   int tile, go, first, gid;
+  int mdefer;  // the key read before the neighbourhood was ready is above the threshold
   unsigned key;
+  unsigned tsw;  // the tile's state word without its pending bits, as of the visit's start
   unsigned upd;  // node updates of the current visit
 };
 
@@ -154,26 +166,107 @@ __device__ __forceinline__ void halo_rc(int k, int &r, int &c) {
   else { r = 1 + (k - 2 * TW - TS); c = TW - 1; }
 }
 
+// Tile state word: pending-round bits 0..7 (bit r mod 8 set while the tile
+// is queued for round r and that round's visit has not finished), the
+// parity of the buffer holding its latest version (bit 8) and the round that
+// version was written in (bits 9..31).
+constexpr unsigned kPendMask = 0xffu;
+constexpr unsigned kPrevDone = 0x80000000u;  // TileSlot::done: the previous round is complete
+__device__ __forceinline__ bool pending_in(unsigned st, int r) { return (st >> (r & 7)) & 1u; }
+
 // Buffer holding a tile's version as of the start of round r.
 __device__ __forceinline__ int start_parity(unsigned st, int r) {
-  const int par = (int)(st & 1u);
-  return ((int)(st >> 1) == r) ? 1 - par : par;
+  const int par = (int)((st >> 8) & 1u);
+  return ((int)(st >> 9) == r) ? 1 - par : par;
 }
 
+__device__ __forceinline__ TileSlot &slot_of(const TileWork &w, int r) {
+  return reinterpret_cast<TileSlot *>(w.ctrl)[r % kSlots];
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void fence_sc() { asm volatile("fence.sc.gpu;" ::: "memory"); }
+
+// Append tile t to round rr's list unless it is already pending there.  The
+// entry carries its round, so a reader never takes a stale entry of the
+// slot's previous round.
 __device__ __forceinline__ void enqueue(const TileWork &w, int ntiles, int t, int rr) {
-  if (atomicMax(&w.queued[t], (unsigned)rr) < (unsigned)rr) {
-    TileSlot *s = reinterpret_cast<TileSlot *>(w.ctrl) + (rr % kSlots);
-    const unsigned idx = atomicAdd(&s->count, 1u);
-    w.list[(size_t)(rr % kSlots) * ntiles + idx] = t;
+  const unsigned bit = 1u << (rr & 7);
+  if (!(atomicOr(&w.tstate[t], bit) & bit)) {
+    const unsigned idx = atomicAdd(&slot_of(w, rr).count, 1u);
+    st_release_u64(&w.list[(size_t)(rr % kSlots) * ntiles + idx], ((unsigned long long)rr << 32) | (unsigned)t);
   }
 }
 
 // Queue tile t for round rr with key bits kb.
 __device__ __forceinline__ void push(const TileWork &w, int ntiles, int t, int rr, unsigned kb) {
-  atomicMin(&w.key[(size_t)(rr & 1) * ntiles + t], kb);
-  TileSlot *s = reinterpret_cast<TileSlot *>(w.ctrl) + (rr % kSlots);
-  atomicMin(&s->kmin, kb);
+  atomicMin(&w.key[(size_t)(rr % kKeySlots) * ntiles + t], kb);
+  atomicMin(&slot_of(w, rr).kmin, kb);
   enqueue(w, ntiles, t, rr);
+}
+
+__device__ __forceinline__ void reset_slot(TileSlot &s, int r) {
+  s.round = 0xffffffffu;  // readers that see a reset field see this first
+  __threadfence();
+  s.count = 0u;
+  s.kmin = kInfBits;
+  s.done = 0u;
+  s.moved = 0u;
+  s.round = (unsigned)r;
+  __threadfence();
+  s.take = (unsigned long long)(unsigned)r << 32;
+}
+
+// Round completion.  Round q is complete when round q - 1 is and all its
+// entries are done; both facts meet in one word: every finished entry adds 1
+// to TileSlot::done, and the completer of q - 1, which knows the final entry
+// count n of q, adds kPrevDone - n, so the word equals kPrevDone exactly when
+// both happened, and exactly one atomic (the last of them) produces that
+// value: its thread completes the round.  The completer
+// decides on round q + 1, whose list is final now (converged: q + 1 would
+// certify after a certification round q that moved nothing; stop at the
+// round cap), readies the slot of round q + 4, publishes the completion and
+// passes kPrevDone on to round q + 1, completing that round too if its
+// entries are all done already.
+__device__ void complete_round(const TileWork &w, int q, int ntiles_all, int max_rounds) {
+  unsigned *ctrl = w.ctrl;
+  for (int guard = 0; guard < (1 << 20); ++guard, ++q) {
+    __threadfence();  // every entry's effects, seen through the done word, before what follows
+    TileSlot &s = slot_of(w, q);
+    const unsigned cnt = __ldcg(&s.count);
+    const unsigned cnt1 = __ldcg(&slot_of(w, q + 1).count);
+    if (cnt == 0u && cnt1 == 0u && __ldcg(&s.moved) == 0u) {
+      ctrl[kCtrlRounds] = (unsigned)q;
+      ctrl[kCtrlStop] = 1u;
+    } else if (q + 1 > max_rounds) {
+      ctrl[kCtrlRounds] = (unsigned)q;
+      ctrl[kCtrlStop] = 2u;
+    }
+    reset_slot(slot_of(w, q + 4), q + 4);
+    __threadfence();
+    st_release_u32(&ctrl[kCtrlComplete], (unsigned)q);
+    const unsigned n1 = cnt1 ? cnt1 : (unsigned)ntiles_all;
+    const unsigned old = atomicAdd(&slot_of(w, q + 1).done, kPrevDone - n1);
+    if (old + (kPrevDone - n1) != kPrevDone) return;
+  }
+}
+
+// End of an entry of round rg (a visit or a deferral), by one thread after
+// the group's stores and queue pushes: the tile is no longer pending in rg,
+// and the round counts the entry.
+// End of an entry of round rg (a visit or a deferral), by one thread after
+// the group's stores and queue pushes, in two halves so that the group's
+// next ticket is requested while the count is in flight: the tile is no
+// longer pending in rg, and the round counts the entry.
+__device__ __forceinline__ unsigned finish_begin(const TileWork &w, int t, int rg) {
+  __threadfence();  // the group's stores and pushes, ordered by its barrier, before both words
+  atomicAnd(&w.tstate[t], ~(1u << (rg & 7)));
+  return atomicAdd(&slot_of(w, rg).done, 1u);
+}
+__device__ __forceinline__ void finish_end(const TileWork &w, int rg, unsigned old, int ntiles_all, int max_rounds) {
+  if (old + 1u == kPrevDone) complete_round(w, rg, ntiles_all, max_rounds);
 }
 
 template <int TS>
@@ -195,170 +288,262 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
   const int NT = (int)w.ctrl[kCtrlNT];  // tiles of all grids
   const int NC = a.ntiles_cap;          // stride of the per-round queue arrays
   const long long plane = a.plane;
-  TileSlot *slots = reinterpret_cast<TileSlot *>(w.ctrl);
-  unsigned *moved_ct = w.ctrl + kCtrlMoved;
   unsigned long long my_warp_evals = 0;
-  bool converged = false, abort = false, prev_cert = false;
-  int r = 1;
+  bool abort = false;
+  // Rounds without a grid barrier: a group takes entries of its round rg
+  // until the round's list is final and exhausted, then moves to rg + 1.  A
+  // taken tile waits until no tile of its 3 x 3 neighbourhood is pending in
+  // round rg - 1; its visit then reads exactly the versions the neighbourhood
+  // had at the end of round rg - 1, as with a barrier between rounds, so the
+  // result does not depend on timing.  Rounds rg and rg + 1 overlap.
+  int rg = 1;
+  int fin_t = -1, fin_rg = 0;  // thread 0: an entry whose end is still to be counted
+  unsigned long long pre = 0ull;  // thread 0: a ticket of round rg requested during the last visit
+  bool have_pre = false;
 
-  for (;; ++r) {
-    TileSlot *cur = slots + (r % kSlots);
-    if (blockIdx.x == 0 && tid == 0) {
-      // the slot last used two rounds ago is free: ready it for round r + 2
-      TileSlot *old = slots + ((r + 2) % kSlots);
-      old->count = 0;
-      old->grab = 0;
-      old->kmin = kInfBits;
-      // round r - 2's moved count was read at the start of round r - 1
-      moved_ct[(r + 1) % kSlots] = 0u;
-    }
-    unsigned n = __ldcg(&cur->count);
-    // an empty queue: done if the previous round certified without a change,
-    // else certify (every tile, every node evaluated)
-    const bool cert = n == 0;
-    if (cert) {
-      if (prev_cert && __ldcg(&moved_ct[(r + 2) % kSlots]) == 0u) {
-        converged = true;
-        break;
+  while (true) {
+    if (gt == 0) {
+      // code: 0 list entry, 1 certification entry, 2 nothing more in round
+      // rg for this group, 3 stop (converged, round cap, timeout)
+      int code = -1, t = -1;
+      unsigned k = 0;
+      TileSlot &sl = slot_of(w, rg);
+      {
+        // a ticket: the next list index of round rg.  A slot is reset for
+        // its next round only once round rg + 4 is complete, and round rg
+        // cannot complete before this group's previous entry of it did, so
+        // the tag check below never fails for a group that just finished
+        // an entry; it guards a group arriving from an older round.
+        unsigned fold = 0u;
+        const int frg = fin_rg;
+        if (fin_t >= 0) fold = finish_begin(w, fin_t, fin_rg);
+        const unsigned long long v = have_pre ? pre : atomicAdd(&sl.take, 1ull);
+        have_pre = false;
+        if (fin_t >= 0) {
+          // before any wait: the round may be waiting for this count
+          finish_end(w, frg, fold, NT, a.max_rounds);
+          fin_t = -1;
+        }
+        if ((unsigned)(v >> 32) != (unsigned)rg) code = 2;
+        k = (unsigned)v;
       }
-      n = (unsigned)NT;
+      const unsigned long long t0 = gtimer();
+      for (unsigned spins = 0; code < 0; ++spins) {
+        // the entry itself first: its tag names the round that wrote it
+        if (k < (unsigned)NC) {
+          const unsigned long long e = ld_acquire_u64(&w.list[(size_t)(rg % kSlots) * NC + k]);
+          if ((unsigned)(e >> 32) == (unsigned)rg) {
+            t = (int)(unsigned)e;
+            code = 0;
+            break;
+          }
+        }
+        // loads after an acquire are ordered after it
+        const int comp = (int)ld_acquire_u32(&w.ctrl[kCtrlComplete]);
+        const unsigned stop = __ldcg(&w.ctrl[kCtrlStop]);
+        const unsigned cnt = __ldcg(&sl.count);
+        const unsigned srnd = __ldcg(&sl.round);
+        if (stop || ld_acquire_s32(a.ctl.abort)) {
+          code = 3;
+          break;
+        }
+        if (comp >= rg || srnd != (unsigned)rg) {  // round rg complete: every entry was taken
+          code = 2;
+          break;
+        }
+        if (comp >= rg - 1) {  // round rg's list is final
+          if (cnt == 0u) {
+            // an empty list: certification round (its tiles are not marked
+            // pending, so no group moves past it before it completes: that
+            // wait ends through comp >= rg above)
+            if (k < (unsigned)NT) {
+              t = (int)k;
+              code = 1;
+              break;
+            }
+          } else if (k >= cnt) {
+            code = 2;
+            break;
+          }
+        }
+        if ((spins & 15u) == 15u && (long long)(gtimer() - t0) > a.ctl.timeout_ns) {
+          raise_timeout(a.ctl);
+          code = 3;
+          break;
+        }
+        __nanosleep(64);
+      }
+      S.go = code;
+      S.tile = t;
+      S.key = 0u;
+      if (t >= 0) {
+        const int gid = a.n_grids == 1 ? 0 : __ldg(&w.tile_grid[t]);
+        S.gid = gid;
+        S.gd = w.grids[gid];
+      }
     }
-    prev_cert = cert;
-    if (r > a.max_rounds) break;
-    const float theta = cert ? kInf : __uint_as_float(__ldcg(&cur->kmin)) + a.window;
-
-    // the first list entry of every group is its own (no atomic at the start
-    // of a round, where all groups would contend for one counter); later
-    // entries are handed out by the counter
-    bool first_take = true;
-    while (true) {
+    group_sync<NG>(bar);
+    const int code = S.go;
+    if (code == 3) break;
+    if (code == 2) {
+      // on to the next round (or past rounds completed meanwhile)
+      if (gt == 0) S.tile = max(rg + 1, (int)ld_acquire_u32(&w.ctrl[kCtrlComplete]) + 1);
+      group_sync<NG>(bar);
+      rg = S.tile;
+      group_sync<NG>(bar);
+      continue;
+    }
+    const int t = S.tile;
+    const bool cert = code == 1;
+    const int gid = S.gid;
+    const TGrid &gd = S.gd;
+    const int tl = t - gd.tile_off;
+    const int ti = tl / gd.tnx, tj = tl - ti * gd.tnx;
+    const int i0 = ti * TS, j0 = tj * TS;
+    const int gny = gd.ny, gnx = gd.nx;
+    const long long goff = gd.node_off;
+    const int i = i0 + row, j = j0 + col;
+    const bool inb = (i < gny) && (j < gnx);
+    const long long p = goff + (long long)i * gnx + j;
+    // the inputs that no visit writes first: fields, source flag, the halo
+    // this tile saw at its previous visit
+    float fl[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    bool is_src = false;
+    if (inb) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fl[c] = __ldg(a.f + c * plane + p);
+      is_src = a.src[p] != 0;
+    }
+    int hr = 0, hc = 0, gi = -1, gj = -1;
+    float prev = kInf;
+    float *hp = nullptr;
+    if (gt < G::HALO) {
+      halo_rc<TS>(gt, hr, hc);
+      gi = i0 - 1 + hr;
+      gj = j0 - 1 + hc;
+      hp = w.halo + (size_t)t * G::HALO + gt;
+      prev = __ldcg(hp);
+    }
+    // readiness: no tile of the 3 x 3 neighbourhood (index (di + 1) * 3 +
+    // (dj + 1)) pending in round rg - 1; the same words give the buffer
+    // parities as of the round's start
+    if (gt < 9) {
+      const int ni = ti + gt / 3 - 1, nj = tj + gt % 3 - 1;
+      int pp = 0;
+      if (ni >= 0 && ni < gd.tny && nj >= 0 && nj < gd.tnx) {
+        const unsigned *sp = &w.tstate[gd.tile_off + ni * gd.tnx + nj];
+        unsigned st = ld_acquire_u32(sp);
+        const unsigned long long t0 = gtimer();
+        for (unsigned spins = 0; pending_in(st, rg - 1); ++spins) {
+          if ((spins & 15u) == 15u &&
+              ((long long)(gtimer() - t0) > a.ctl.timeout_ns || ld_acquire_s32(a.ctl.abort))) {
+            raise_timeout(a.ctl);
+            break;
+          }
+          __nanosleep(32);
+          st = ld_acquire_u32(sp);
+        }
+        pp = start_parity(st, rg);
+        if (gt == 4) S.tsw = st & ~kPendMask;
+      }
+      S.par[gt] = pp;
+      S.nkey[gt] = kInfBits;
+    }
+    unsigned nvis = 0u;
+    if (gt == 9) {
+      nvis = __ldcg(&w.visits[t]);
+      S.first = nvis == 0u;
+    }
+    if (gt == 10) {
+      // keys only decrease: a key already at or below the threshold stays so
+      int md = 0;
+      if (!cert) {
+        const unsigned k0 = __ldcg(&w.key[(size_t)(rg % kKeySlots) * NC + t]);
+        md = __uint_as_float(k0) > __uint_as_float(ld_acquire_u32(&slot_of(w, rg - 1).kmin)) + a.window;
+      }
+      S.mdefer = md;
+    }
+    if (gt < G::TW) {
+      S.rowm[0][gt] = 0ull;
+      S.rowm[1][gt] = 0ull;
+    }
+    if (gt == 0) S.upd = 0u;
+    group_sync<NG>(bar);
+    if (S.mdefer) {
+      // likely too far ahead of the front: decide on the final key (only the
+      // neighbourhood's round rg - 1 visits queue this tile for round rg, and
+      // they are done) before anything else is loaded
       if (gt == 0) {
-        const unsigned ngroups = gridDim.x * G::GROUPS;
-        const unsigned k = first_take ? blockIdx.x * G::GROUPS + grp : ngroups + atomicAdd(&cur->grab, 1u);
-        S.go = k < n;
-        int t = -1;
-        if (k < n && cert) {
-          t = (int)k;
-          S.key = 0u;
-        } else if (k < n) {
-          t = __ldcg(&w.list[(size_t)(r % kSlots) * NC + k]);
-          unsigned *kp = &w.key[(size_t)(r & 1) * NC + t];
-          S.key = __ldcg(kp);
+        unsigned *kp = &w.key[(size_t)(rg % kKeySlots) * NC + t];
+        const unsigned kbits = __ldcg(kp);
+        const float theta = __uint_as_float(ld_acquire_u32(&slot_of(w, rg - 1).kmin)) + a.window;
+        int defer = 0;
+        if (__uint_as_float(kbits) > theta) {
+          // keep it for a later round
           __stcg(kp, kInfBits);
+          push(w, NC, t, rg + 1, kbits);
+          fin_t = t;
+          fin_rg = rg;
+          defer = 1;
         }
-        if (t >= 0) {
-          // the tile's grid, kept in shared memory for the visit
-          const int gid = a.n_grids == 1 ? 0 : __ldg(&w.tile_grid[t]);
-          S.tile = t;
-          S.gid = gid;
-          S.gd = w.grids[gid];
-        }
+        S.go = defer;
       }
       group_sync<NG>(bar);
-      first_take = false;
-      if (!S.go) break;
-      const int t = S.tile;
-      const unsigned kb = S.key;
-      if (__uint_as_float(kb) > theta) {
-        // too far ahead of the front: keep it for a later round
-        if (gt == 0) push(w, NC, t, r + 1, kb);
-        group_sync<NG>(bar);
-        continue;
-      }
-      const int gid = S.gid;
-      const TGrid &gd = S.gd;
-      const int tl = t - gd.tile_off;
-      const int ti = tl / gd.tnx, tj = tl - ti * gd.tnx;
-      const int i0 = ti * TS, j0 = tj * TS;
-      const int gny = gd.ny, gnx = gd.nx;
-      const long long goff = gd.node_off;
-      // Everything that does not depend on the neighbours' buffer parities is
-      // requested first, so that a visit pays two dependent global round
-      // trips (parities, then T) instead of one per step.
-      const int i = i0 + row, j = j0 + col;
-      const bool inb = (i < gny) && (j < gnx);
-      const long long p = goff + (long long)i * gnx + j;
-      float fl[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      bool is_src = false;
-      if (inb) {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) fl[c] = __ldg(a.f + c * plane + p);
-        is_src = a.src[p] != 0;
-      }
-      int hr = 0, hc = 0, gi = -1, gj = -1;
-      float prev = kInf;
-      float *hp = nullptr;
-      // T of the node and of its halo node from both buffers, before the
-      // parities are known: the round-start buffer of a tile is not written
-      // during the round, so the one selected below is current
-      float tb0 = kInf, tb1 = kInf, hv0 = kInf, hv1 = kInf;
-      if (inb) {
-        tb0 = __ldcg(a.T[0] + p);
-        tb1 = __ldcg(a.T[1] + p);
-      }
-      if (gt < G::HALO) {
-        halo_rc<TS>(gt, hr, hc);
-        gi = i0 - 1 + hr;
-        gj = j0 - 1 + hc;
-        hp = w.halo + (size_t)t * G::HALO + gt;
-        prev = __ldcg(hp);
-        if (gi >= 0 && gi < gny && gj >= 0 && gj < gnx) {
-          const long long hq = goff + (long long)gi * gnx + gj;
-          hv0 = __ldcg(a.T[0] + hq);
-          hv1 = __ldcg(a.T[1] + hq);
-        }
-      }
-      // buffer parities of this tile and its eight neighbours as of the
-      // round's start (index (di + 1) * 3 + (dj + 1)); the first-visit flag
-      if (gt < 9) {
-        const int di = gt / 3 - 1, dj = gt % 3 - 1;
-        const int ni = ti + di, nj = tj + dj;
-        int pp = 0;
-        if (ni >= 0 && ni < gd.tny && nj >= 0 && nj < gd.tnx)
-          pp = start_parity(__ldcg(&w.tstate[gd.tile_off + ni * gd.tnx + nj]), r);
-        S.par[gt] = pp;
-        S.nkey[gt] = kInfBits;
-      }
-      if (gt == 9) S.first = __ldcg(&w.visits[t]) == 0u;
-      if (gt < G::TW) {
-        S.rowm[0][gt] = 0ull;
-        S.rowm[1][gt] = 0ull;
-      }
-      if (gt == 0) S.upd = 0u;
-      // this thread's node: cone-form constants into shared memory
-      if (inb) {
-        float4 q[kPlanes];
-        node_record(fl[0], fl[1], fl[2], fl[3], fl[4], gd.h, a.eps, is_src, q);
-#pragma unroll
-        for (int c = 0; c < kPlanes; ++c) S.q[c][gt] = q[c];
-      }
+      const int deferred = S.go;
       group_sync<NG>(bar);
-      const int pt = S.par[4];
-      float *Tout = a.T[1 - pt];
-      float tcur = pt ? tb1 : tb0;
-      // halo ring, from the neighbours' round-start versions; nodes whose
-      // value differs from this tile's previous visit seed the change masks
-      if (gt < G::HALO) {
-        const int di = (hr == 0) ? -1 : (hr == G::TW - 1) ? 1 : 0;
-        const int dj = (hc == 0) ? -1 : (hc == G::TW - 1) ? 1 : 0;
-        const float v = S.par[(di + 1) * 3 + dj + 1] ? hv1 : hv0;
-        S.Ts[0][hr][hc] = v;
-        S.Ts[1][hr][hc] = v;
-        if (node_changed(v, prev, a.tol, a.rtol)) atomicOr(&S.rowm[0][hr], frame_bit<TS>(hc));
-        __stcg(hp, v);
+      if (deferred) continue;
+    }
+    // T of the node and of its halo node from the round-start buffers
+    const int pt = S.par[4];
+    float *Tout = a.T[1 - pt];
+    float tcur = inb ? __ldcg(a.T[pt] + p) : kInf;
+    float hv = kInf;
+    if (gt < G::HALO && gi >= 0 && gi < gny && gj >= 0 && gj < gnx) {
+      const int di = (hr == 0) ? -1 : (hr == G::TW - 1) ? 1 : 0;
+      const int dj = (hc == 0) ? -1 : (hc == G::TW - 1) ? 1 : 0;
+      hv = __ldcg(a.T[S.par[(di + 1) * 3 + dj + 1]] + goff + (long long)gi * gnx + gj);
+    }
+    if (gt == 0) {
+      // the final key (within the threshold now), kept for a capped visit
+      unsigned kbits = 0u;
+      if (!cert) {
+        unsigned *kp = &w.key[(size_t)(rg % kKeySlots) * NC + t];
+        kbits = __ldcg(kp);
+        __stcg(kp, kInfBits);
       }
-      const bool upd = inb && !is_src;
-      S.t0[gt] = tcur;
-      S.Ts[0][sr][sc] = tcur;
-      S.Ts[1][sr][sc] = tcur;
-      // first visit: the sources (cold) or every node (warm) start changed;
-      // a certification visit evaluates every node
-      if (S.first || cert) {
-        const bool seed = inb && (a.warm || cert || is_src);
-        const unsigned bal = __ballot_sync(0xffffffffu, seed);
-        const unsigned long long byte = (bal >> (8 * ao)) & 0xffu;
-        if ((lane & 7) == 0 && byte) atomicOr(&S.rowm[0][sr], byte << (8 * pc));
-      }
+      S.key = kbits;
+    }
+    // this thread's node: cone-form constants into shared memory
+    if (inb) {
+      float4 q[kPlanes];
+      node_record(fl[0], fl[1], fl[2], fl[3], fl[4], gd.h, a.eps, is_src, q);
+#pragma unroll
+      for (int c = 0; c < kPlanes; ++c) S.q[c][gt] = q[c];
+    }
+    group_sync<NG>(bar);
+    const unsigned kb = S.key;
+    if (gt == 9) __stcg(&w.visits[t], nvis + 1u);
+    // halo ring, from the neighbours' round-start versions; nodes whose
+    // value differs from this tile's previous visit seed the change masks
+    if (gt < G::HALO) {
+      const float v = hv;
+      S.Ts[0][hr][hc] = v;
+      S.Ts[1][hr][hc] = v;
+      if (node_changed(v, prev, a.tol, a.rtol)) atomicOr(&S.rowm[0][hr], frame_bit<TS>(hc));
+      __stcg(hp, v);
+    }
+    const bool upd = inb && !is_src;
+    S.t0[gt] = tcur;
+    S.Ts[0][sr][sc] = tcur;
+    S.Ts[1][sr][sc] = tcur;
+    // first visit: the sources (cold) or every node (warm) start changed;
+    // a certification visit evaluates every node
+    if (S.first || cert) {
+      const bool seed = inb && (a.warm || cert || is_src);
+      const unsigned bal = __ballot_sync(0xffffffffu, seed);
+      const unsigned long long byte = (bal >> (8 * ao)) & 0xffu;
+      if ((lane & 7) == 0 && byte) atomicOr(&S.rowm[0][sr], byte << (8 * pc));
+    }
       group_sync<NG>(bar);
 
       // Jacobi iterations with the halo fixed
@@ -408,6 +593,11 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
         }
       }
 
+      // the next ticket, requested while this visit publishes
+      if (gt == 0) {
+        pre = atomicAdd(&slot_of(w, rg).take, 1ull);
+        have_pre = true;
+      }
       // publish: a new version only if some node moved beyond the tolerance
       const bool moved = upd && node_changed(tcur, S.t0[gt], a.tol, a.rtol);
       if (group_sync_or<NG>(bar, moved)) {
@@ -428,37 +618,45 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
         }
         group_sync<NG>(bar);
         if (gt == 0) {
-          __stcg(&w.tstate[t], ((unsigned)r << 1) | (unsigned)(1 - pt));
-          atomicAdd(&moved_ct[r % kSlots], 1u);
+          // the new version's round and buffer, leaving the pending bits
+          // (other tiles queue this one concurrently) untouched
+          // (a reader that finds the new round takes the other buffer, the
+          // round-start version; the new values become readable through the
+          // fence before the pending bit is cleared at the entry's end)
+          const unsigned nw = ((unsigned)rg << 9) | ((unsigned)(1 - pt) << 8);
+          atomicXor(&w.tstate[t], S.tsw ^ nw);
+          atomicAdd(&slot_of(w, rg).moved, 1u);
         }
         if (gt < 9 && gt != 4 && S.nkey[gt] != kInfBits) {
           const int ni = ti + gt / 3 - 1, nj = tj + gt % 3 - 1;
+          // the neighbour's visit waits for this entry's end (readiness)
           if (ni >= 0 && ni < gd.tny && nj >= 0 && nj < gd.tnx)
-            push(w, NC, gd.tile_off + ni * gd.tnx + nj, r + 1, S.nkey[gt]);
+            push(w, NC, gd.tile_off + ni * gd.tnx + nj, rg + 1, S.nkey[gt]);
         }
       }
       if (gt == 0) {
-        __stcg(&w.visits[t], __ldcg(&w.visits[t]) + 1u);
         if (S.upd) {
           atomicAdd(&w.gupd[gid], (unsigned long long)S.upd);
           atomicAdd(&w.counters[0], (unsigned long long)S.upd);
         }
         // a visit cut short by the iteration cap is resumed next round
-        if (capped) push(w, NC, t, r + 1, kb);
+        if (capped) push(w, NC, t, rg + 1, kb);
       }
       group_sync<NG>(bar);
-    }
-    if (!grid_sync(a.ctl)) {  // begins with __syncthreads: every group is done
-      abort = true;
-      break;
-    }
+      if (gt == 0) {
+        // counted at the next take
+        fin_t = t;
+        fin_rg = rg;
+      }
   }
   if (lane == 0 && my_warp_evals) atomicAdd(&w.counters[1], my_warp_evals);
+  // one barrier at the end: every group has left the loop
+  if (!grid_sync(a.ctl)) abort = true;
   if (!abort) {
     // hand the latest version of every tile back in the caller's buffer: a
     // tile per group, one thread per node
     for (int t = blockIdx.x * G::GROUPS + grp; t < NT; t += gridDim.x * G::GROUPS) {
-      if ((__ldcg(&w.tstate[t]) & 1u) == 0u) continue;
+      if (((__ldcg(&w.tstate[t]) >> 8) & 1u) == 0u) continue;
       const int gid = a.n_grids == 1 ? 0 : __ldg(&w.tile_grid[t]);
       const TGrid gd = w.grids[gid];
       const int tl = t - gd.tile_off;
@@ -470,7 +668,8 @@ __global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
-    a.ctl.st->rounds = (unsigned)(r - 1);
+    const bool converged = !abort && __ldcg(&w.ctrl[kCtrlStop]) == 1u;
+    a.ctl.st->rounds = __ldcg(&w.ctrl[kCtrlRounds]);
     a.ctl.st->converged = converged ? 1 : 0;
     if (!converged && !abort) set_error(a.ctl.st, RF_ERR_NOT_CONVERGED);
   }
@@ -570,7 +769,10 @@ __global__ void tile_map_kernel(TileWork w) {
     w.tile_grid[g.tile_off + k] = (int)blockIdx.y;
 }
 
-// Workspace reset (tiles_cap tiles) and the slots.
+// Workspace reset (tiles_cap tiles, every round list cleared) and the
+// slots: slot k serves round k,
+// round 0 is complete (the seed kernels fill round 1's list), and its kmin
+// is 0 (round 1's threshold is the window).
 __global__ void tile_reset_kernel(TileArgs a) {
   const TileWork &w = a.w;
   const int NC = a.ntiles_cap;
@@ -580,17 +782,27 @@ __global__ void tile_reset_kernel(TileArgs a) {
   if (g0 == 0) {
     TileSlot *slots = reinterpret_cast<TileSlot *>(w.ctrl);
     for (int k = 0; k < kSlots; ++k) {
+      slots[k].take = (unsigned long long)(unsigned)k << 32;
       slots[k].count = 0u;
-      slots[k].grab = 0u;
-      slots[k].kmin = kInfBits;
+      slots[k].kmin = k == 0 ? 0u : kInfBits;
+      slots[k].done = 0u;  // round 1's share of round 0's completion: tile_finish_seed_kernel
+      slots[k].moved = 0u;
+      slots[k].pad0 = 0u;
+      slots[k].round = (unsigned)k;
     }
+    w.ctrl[kCtrlComplete] = 0u;
+    w.ctrl[kCtrlStop] = 0u;
+    w.ctrl[kCtrlRounds] = 0u;
   }
   for (long long t = g0; t < NC; t += stride) {
-    w.tstate[t] = 0u;
+    w.tstate[t] = a.warm ? (1u << 1) : 0u;  // warm: every tile pending in round 1
     w.visits[t] = 0u;
-    w.key[t] = kInfBits;
-    w.key[NC + t] = kInfBits;
-    w.queued[t] = a.warm ? 1u : 0u;
+#pragma unroll
+    for (int k = 0; k < kKeySlots; ++k) w.key[(size_t)k * NC + t] = kInfBits;
+    // no entry of an earlier solve may carry a round of this one: a reader
+    // that runs ahead of a producer's store must see a foreign tag
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) w.list[(size_t)k * NC + t] = 0ull;
   }
   for (long long k = g0; k < (long long)NC * halo; k += stride) w.halo[k] = kInf;
   for (long long g = g0; g < a.n_grids; g += stride) w.gupd[g] = 0ull;
@@ -625,7 +837,7 @@ __global__ void tile_seed_kernel(TileArgs a) {
         const int ii = i + di, jj = j + dj;
         if (ii < 0 || ii >= g.ny || jj < 0 || jj >= g.nx) continue;
         const int t = g.tile_off + (ii / a.ts) * g.tnx + jj / a.ts;
-        atomicMin(&w.key[NC + t], 0u);  // round 1 reads key slot 1
+        atomicMin(&w.key[(size_t)(1 % kKeySlots) * NC + t], 0u);
         enqueue(w, NC, t, 1);
       }
   }
@@ -633,8 +845,8 @@ __global__ void tile_seed_kernel(TileArgs a) {
     const int nt = g.tny * g.tnx;
     for (long long k = g0; k < nt; k += stride) {
       const int t = g.tile_off + (int)k;
-      w.key[NC + t] = 0u;
-      w.list[(size_t)(1 % kSlots) * NC + t] = t;
+      w.key[(size_t)(1 % kKeySlots) * NC + t] = 0u;
+      w.list[(size_t)(1 % kSlots) * NC + t] = (1ull << 32) | (unsigned)t;
     }
   }
 #pragma unroll
@@ -660,6 +872,9 @@ __global__ void tile_finish_seed_kernel(TileArgs a) {
     TileSlot *slots = reinterpret_cast<TileSlot *>(w.ctrl);
     if (a.warm) slots[1 % kSlots].count = w.ctrl[kCtrlNT];
     slots[1 % kSlots].kmin = 0u;
+    // round 0 is complete: round 1's list is final (an empty one certifies)
+    const unsigned n1 = slots[1 % kSlots].count ? slots[1 % kSlots].count : w.ctrl[kCtrlNT];
+    slots[1 % kSlots].done = kPrevDone - n1;
   }
 }
 
@@ -700,10 +915,10 @@ int tiles_cap(int n_grids, long long total_nodes, int max_line, int ts) {
 
 size_t tile_work_bytes(int n_grids, int ntiles_cap, int ts) {
   const size_t NC = (size_t)ntiles_cap;
-  // counters, ctrl, grids, per-grid updates, then tstate, visits, queued,
-  // key[2], list[3], tile -> grid, halo
-  return 64 + 256 + (size_t)n_grids * sizeof(TGrid) + (size_t)n_grids * 8 + NC * 4 * 5 + NC * 4 * kSlots +
-         NC * 4 + NC * (size_t)(4 * ts + 4) * 4;
+  // counters, ctrl, grids, per-grid updates, list[8] (8-byte entries), then
+  // tstate, visits, key[4], tile -> grid, halo
+  return 64 + kCtrlBytes + (size_t)n_grids * sizeof(TGrid) + (size_t)n_grids * 8 + NC * 8 * kSlots + NC * 4 * 2 +
+         NC * 4 * kKeySlots + NC * 4 + NC * (size_t)(4 * ts + 4) * 4;
 }
 
 TileWork tile_work_carve(void *base, int n_grids, int ntiles_cap, int ts) {
@@ -712,22 +927,20 @@ TileWork tile_work_carve(void *base, int n_grids, int ntiles_cap, int ts) {
   TileWork w;
   w.counters = (unsigned long long *)b;  // 8-byte aligned first
   b += 64;
-  w.ctrl = (unsigned *)b;
-  b += 256;
+  w.ctrl = (unsigned *)b;  // the slots' 64-bit words stay 8-byte aligned
+  b += kCtrlBytes;
   w.grids = (TGrid *)b;  // 8-byte aligned
   b += (size_t)n_grids * sizeof(TGrid);
   w.gupd = (unsigned long long *)b;
   b += (size_t)n_grids * 8;
+  w.list = (unsigned long long *)b;
+  b += NC * 8 * kSlots;
   w.tstate = (unsigned *)b;
   b += NC * 4;
   w.visits = (unsigned *)b;
   b += NC * 4;
-  w.queued = (unsigned *)b;
-  b += NC * 4;
   w.key = (unsigned *)b;
-  b += NC * 8;
-  w.list = (int *)b;
-  b += NC * 4 * kSlots;
+  b += NC * 4 * kKeySlots;
   w.tile_grid = (int *)b;
   b += NC * 4;
   w.halo = (float *)b;
@@ -771,7 +984,7 @@ rf_status tiles_launch(const TileLaunch &L, const TileWork &w, const LaunchCtl &
   a.max_local = 16 * ts;
   a.w = w;
   a.ctl = ctl;
-  if (cudaMemsetAsync(w.counters, 0, 64 + 256, s) != cudaSuccess) return RF_ERR_CUDA;
+  if (cudaMemsetAsync(w.counters, 0, 64 + kCtrlBytes, s) != cudaSuccess) return RF_ERR_CUDA;
   if (L.descs) {
     tile_plan_batch_kernel<<<1, 1024, 0, s>>>(w, L.descs, L.n_grids, ts, L.total_nodes, L.max_line, L.ntiles_cap,
                                               ctl.st);

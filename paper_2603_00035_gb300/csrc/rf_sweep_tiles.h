@@ -23,14 +23,14 @@ struct TGrid {
 // Per-solve workspace of the tile queue (one device allocation, carved).
 struct TileWork {
   unsigned long long *counters;  // [0] node updates, [1] warp evaluations
-  unsigned *ctrl;                // round slots (count, grab, kmin, pad) x 3, tile count, spare, moved [3]
+  unsigned *ctrl;                // round slots x 8, tile count, completed round, stop flag, rounds
   TGrid *grids;                  // [grids]
   unsigned long long *gupd;      // [grids] node updates per grid
-  unsigned *tstate;              // per tile: (round last written << 1) | buffer parity
+  unsigned long long *list;      // [8][tiles cap] queued tiles (round << 32 | tile), by round mod 8
+  unsigned *tstate;              // per tile: (round last written << 9) | (buffer parity << 8) | pending rounds
+                                 // (bit r mod 8: queued for round r and not yet done)
   unsigned *visits;              // per tile: visits so far
-  unsigned *queued;              // per tile: last round it was queued for
-  unsigned *key;                 // [2][tiles cap] float bits of the queue key, by round parity
-  int *list;                     // [3][tiles cap] queued tiles, by round mod 3
+  unsigned *key;                 // [4][tiles cap] float bits of the queue key, by round mod 4
   int *tile_grid;                // [tiles cap] grid of each tile (batches)
   float *halo;                   // [tiles cap][4 * ts + 4] halo seen at the previous visit
 };
