@@ -20,14 +20,21 @@
 //    warp and row);
 //  * a tile whose boundary nodes changed queues its neighbours for the next
 //    round, keyed by the smallest new boundary time; a round processes the
-//    queued tiles whose key is within a window of the smallest key and
-//    defers the others (delta-stepping on tiles: tiles far ahead of the
-//    front would only be revisited once the front reaches them);
+//    queued tiles whose key is within a window of the previous round's
+//    smallest key and defers the others (delta-stepping on tiles: tiles far
+//    ahead of the front would only be revisited once the front reaches them);
 //  * tiles read their neighbours' state as of the start of the round: every
 //    tile's latest version lives in one of two T buffers, tagged per tile
 //    with (round written, parity); a tile writes its new version into the
 //    other buffer, so results do not depend on the order in which tiles are
 //    taken, and the solve is deterministic;
+//  * there is no grid barrier between rounds: a group moves on to round r + 1
+//    once round r's list is final (round r - 1 complete) and handed out, and
+//    a tile of round r + 1 starts once no tile of its 3 x 3 neighbourhood is
+//    pending in round r (a pending-round bit per tile and round mod 8), so it
+//    reads exactly what a barrier would have given it while the slowest
+//    visits of round r still run elsewhere; a round's completion is counted
+//    in one word per round (see complete_round);
 //  * when a round queues nothing, the next round certifies: it visits every
 //    tile with every node marked changed, so each node is evaluated once with
 //    the current values (a change below the tolerance never marks its
