@@ -459,6 +459,17 @@ rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, int H,
 rf_status rf_unet_conv3x3_wgrad(rf_ctx *ctx, const uint16_t *x,
                                 const uint16_t *dy, int B, int H, int W,
                                 int Cin, int Cout, float *dw, void *stream);
+/* The same weight gradient on the fifth-generation tensor cores: per tap a
+ * GEMM (M = output channels, N = input channels, K = pixels) with both BF16
+ * operands staged in shared memory as they lie in memory (MN-major) and
+ * the 9 FP32 accumulators in tensor memory; partial sums over pixel-row
+ * ranges are added to dw (the caller zeroes it).  Cin, Cout multiples of
+ * 16; x, dy 16-byte aligned (else RF_ERR_INVALID_ARG).  A tensor-core wait
+ * beyond the context timeout sets RF_ERR_TIMEOUT in the statistics. */
+rf_status rf_unet_conv3x3_wgrad_tc(rf_ctx *ctx, const uint16_t *x,
+                                   const uint16_t *dy, int B, int H, int W,
+                                   int Cin, int Cout, float *dw,
+                                   void *stream);
 /* db [C] (FP32) += sum over npix pixels of dy [npix][C]. */
 rf_status rf_unet_bias_grad(rf_ctx *ctx, const uint16_t *dy, int64_t npix,
                             int C, float *db, void *stream);

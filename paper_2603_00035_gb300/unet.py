@@ -49,6 +49,16 @@ def conv3x3(lib, h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s):
     return fn(h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s)
 
 
+def conv3x3_wgrad(lib, h, x, dy, B, H, W, Cin, Cout, dw, s):
+    """rf_unet_conv3x3_wgrad on the tcgen05 kernel for 128 or more output
+    channels, where it measured faster on GB300 (153-202 vs 140-150 TFLOP/s:
+    8 x 128^2 at 128 -> 128, 8 x 64^2 at 256 -> 256 and 384 -> 128), and on
+    the mma.sync kernel for the narrow layers (82-130 vs 44-75 TFLOP/s at
+    16-64 output channels: the tensor-core tile is 128 output channels)."""
+    fn = lib.rf_unet_conv3x3_wgrad_tc if Cout % 128 == 0 else lib.rf_unet_conv3x3_wgrad
+    return fn(h, x, dy, B, H, W, Cin, Cout, dw, s)
+
+
 class UNet:
     def __init__(self, cin=16, base=32, cout=16, device="cuda", seed=0, ctx=None, plan=None):
         """plan: a layer list in layer_plan's format (the last convolution
@@ -163,7 +173,7 @@ class UNet:
                 if relu:
                     g = g.clone()
                     _chk(lib.rf_unet_relu_backward(h, _ptr(g), _ptr(y), g.numel(), s), "relu_bwd")
-                _chk(lib.rf_unet_conv3x3_wgrad(h, _ptr(xin), _ptr(g), B_, H_, W_, ci, co, _ptr(self.gW[name]), s),
+                _chk(conv3x3_wgrad(lib, h, _ptr(xin), _ptr(g), B_, H_, W_, ci, co, _ptr(self.gW[name]), s),
                      "wgrad")
                 _chk(lib.rf_unet_bias_grad(h, _ptr(g), B_ * H_ * W_, co, _ptr(self.gb[name]), s), "bias_grad")
                 if name == self.plan[0][0]:
@@ -244,6 +254,29 @@ def bench_conv(B=8, H=128, W=128, Cin=128, Cout=128, reps=20, tensor_cores=True)
     return ms, 2.0 * B * H * W * Cout * 9 * Cin / (ms * 1e-3) / 1e12
 
 
+def bench_wgrad(B, H, W, Cin, Cout, reps=20, tensor_cores=True):
+    """Time the weight gradient of one 3x3 layer (rf_unet_conv3x3_wgrad_tc,
+    or the mma.sync rf_unet_conv3x3_wgrad) on random data, the accumulator
+    zeroed before each call.  Returns (ms per call, TFLOP/s)."""
+    lib, s, ctx = L.load(), _stream(), Context.get(0)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((B, H, W, Cin), generator=g).to(torch.bfloat16).cuda()
+    dy = torch.randn((B, H, W, Cout), generator=g).to(torch.bfloat16).cuda()
+    dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+    fn = lib.rf_unet_conv3x3_wgrad_tc if tensor_cores else lib.rf_unet_conv3x3_wgrad
+    call = lambda: _chk(fn(ctx.handle, _ptr(x), _ptr(dy), B, H, W, Cin, Cout, _ptr(dw), s), "wgrad")
+    for _ in range(3):
+        call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return ms, 2.0 * B * H * W * Cout * 9 * Cin / (ms * 1e-3) / 1e12
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -252,6 +285,9 @@ if __name__ == "__main__":
     p.add_argument("--shape", type=int, nargs=5, default=[8, 128, 128, 128, 128], metavar=("B", "H", "W", "CIN", "COUT"))
     p.add_argument("--reps", type=int, default=20)
     p.add_argument("--mma-sync", action="store_true", help="time the mma.sync kernel instead of tcgen05")
+    p.add_argument("--wgrad", action="store_true", help="time the weight gradient instead of the convolution")
     a = p.parse_args()
-    ms, tf = bench_conv(*a.shape, reps=a.reps, tensor_cores=not a.mma_sync)
-    print(json.dumps({"shape": a.shape, "kernel": "mma.sync" if a.mma_sync else "tcgen05", "ms": ms, "tflops": tf}))
+    bench = bench_wgrad if a.wgrad else bench_conv
+    ms, tf = bench(*a.shape, reps=a.reps, tensor_cores=not a.mma_sync)
+    print(json.dumps({"shape": a.shape, "op": "wgrad" if a.wgrad else "conv",
+                      "kernel": "mma.sync" if a.mma_sync else "tcgen05", "ms": ms, "tflops": tf}))

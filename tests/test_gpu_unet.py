@@ -101,6 +101,31 @@ def test_conv3x3_tcgen05_forward_and_dgrad(B, H, W, Cin, Cout, relu):
     assert rel(dx32.cpu().numpy(), U.conv3x3_dgrad(dy, w)) < 1e-5
 
 
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [(1, 8, 16, 16, 16), (2, 13, 37, 32, 48), (1, 24, 70, 96, 32),
+                                            (2, 9, 130, 64, 128), (1, 6, 20, 384, 128), (2, 4, 6, 256, 256),
+                                            (3, 5, 64, 48, 144)])
+def test_conv3x3_wgrad_tcgen05(B, H, W, Cin, Cout):
+    """The tcgen05 weight gradient (MN-major BF16 operands, FP32 accumulators
+    in tensor memory, split over pixel rows) against the FP64 reference and
+    the mma.sync kernel: ragged widths (several 64-pixel segments and a
+    partial one), output channels beyond a 128 tile, Cin not a multiple of
+    32 (16-channel tiles)."""
+    rng = np.random.default_rng(B * 7 + H * 3 + Cin)
+    ctx, lib, s = Context.get(0), L.load(), _stream()
+    x_t, x = bf16(rng.standard_normal((B, H, W, Cin)))
+    dy_t, dy = bf16(rng.standard_normal((B, H, W, Cout)))
+    dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+    L.check(lib.rf_unet_conv3x3_wgrad_tc(ctx.handle, _ptr(x_t), _ptr(dy_t), B, H, W, Cin, Cout, _ptr(dw), s),
+            "wgrad_tc")
+    torch.cuda.synchronize()
+    assert ctx.stats()["status"] == 0
+    ref = U.conv3x3_wgrad(x, dy)
+    assert rel(dw.cpu().numpy(), ref) < 1e-5
+    dwm = torch.zeros_like(dw)
+    L.check(lib.rf_unet_conv3x3_wgrad(ctx.handle, _ptr(x_t), _ptr(dy_t), B, H, W, Cin, Cout, _ptr(dwm), s), "wgrad")
+    assert (dw - dwm).abs().max().item() <= 1e-4 * max(1.0, dwm.abs().max().item())
+
+
 def test_pool_upsample_concat_relu_mse():
     rng = np.random.default_rng(7)
     ctx, lib, s = Context.get(0), L.load(), _stream()
