@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "rf_ctx.h"
@@ -445,6 +446,218 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form: one CTA per SM walks the output tiles (8 x 16 pixels x N
+// channels; consecutive tiles share their weights), with two accumulators
+// in tensor memory so that a tile's epilogue overlaps the next tile's MMAs.
+//  * warp 4 (producer): stage after stage, across tiles, as in
+//    conv3x3_tma_kernel (16 input channels per stage, a ring of
+//    persist_stages(N) stages);
+//  * warp 5, lane 0 (MMA issuer): per tile, waits until the epilogue has
+//    released the tile's accumulator (tiles alternate between the two),
+//    issues 9 MMAs per stage, commits each stage to its "empty" barrier and
+//    the tile to the accumulator's "full" barrier;
+//  * warps 0-3 (epilogue; warp w reads TMEM lanes 32w .. 32w+31): wait for
+//    the accumulator, add bias, ReLU, store, and release the accumulator
+//    (one arrival per warp).
+// Every wait is bounded by the context timeout; a timeout records
+// RF_ERR_TIMEOUT, every role leaves its loop, and the CTA waits (bounded)
+// for the MMAs it issued before freeing TMEM.
+__host__ __device__ constexpr int persist_stages(int N) {
+  return (int)((210u * 1024u) / (stage_a_bytes() + stage_b_bytes(N))) > 8
+             ? 8
+             : (int)((210u * 1024u) / (stage_a_bytes() + stage_b_bytes(N)));
+}
+__host__ __device__ constexpr size_t persist_smem_bytes(int N) {
+  return (size_t)persist_stages(N) * (stage_a_bytes() + stage_b_bytes(N)) + (2 * persist_stages(N) + 5) * 8 + 16;
+}
+constexpr int kPersistThreads = 192;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(m)) : "memory");
+}
+
+struct TileIdx {
+  int tx0, ty0, n0, b;
+};
+__device__ __forceinline__ TileIdx tile_of(int tile, int tiles_x, int tiles_pix, int ntn) {
+  TileIdx r;
+  const int pt = tile % tiles_pix, q = tile / tiles_pix;
+  r.n0 = (q % ntn);
+  r.b = q / ntn;
+  r.tx0 = (pt % tiles_x) * kTW;
+  r.ty0 = (pt / tiles_x) * kTH;
+  return r;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    conv3x3_persist_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
+                           TmaArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  constexpr int S = persist_stages(N);
+  constexpr unsigned kCols = (2 * N) < 32 ? 32 : 2 * N;
+  constexpr unsigned SA = stage_a_bytes(), SB = stage_b_bytes(N), SS = SA + SB;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + S * SS);
+  uint64_t *empty = full + S;
+  uint64_t *tfull = empty + S;  // [2]
+  uint64_t *tempty = tfull + 2;  // [2]
+  uint64_t *done = tempty + 2;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  __shared__ int s_late;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_x = (a.W + kTW - 1) / kTW, tiles_pix = tiles_x * ((a.H + kTH - 1) / kTH);
+  const int ntn = a.Cout / N, ntiles = tiles_pix * ntn * a.B;
+  const int nchunks = a.Cin / 16;
+
+  if (warp == 0) tmem_alloc(tslot, kCols);
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&tfull[k], 1);
+      mbar_init(&tempty[k], 4);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+    s_late = 0;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 4) {
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const TileIdx ti = tile_of(tile, tiles_x, tiles_pix, ntn);
+      for (int i = 0; i < nchunks; ++i, ++it) {
+        const int st = it % S;
+        const unsigned u = (unsigned)(it / S);
+        int good = 1;
+        if (lane == 0 && it >= S) good = mbar_wait(&empty[st], (u - 1u) & 1u, a.timeout_ns);
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (!good || *(volatile int *)&s_late) {
+          if (lane == 0) s_late = 1;
+          ok = false;
+          break;
+        }
+        unsigned char *sa = sm + st * SS, *sb = sa + SA;
+        if (lane == 0) mbar_arrive_tx(&full[st], SS);
+        __syncwarp();
+        const int c8_0 = i * 2;
+        if (lane < 6) {
+          const int kx = lane >> 1, c8 = lane & 1;
+          tma_load_4d(sa + (kx * 2 + c8) * kPlaneBytes, &xmap, (c8_0 + c8) * 8, ti.tx0 + kx - 1, ti.ty0 - 1, ti.b,
+                      &full[st]);
+        } else if (lane < 24) {
+          const int j = lane - 6, t = j >> 1, c8 = j & 1;
+          tma_load_3d(sb + (t * 2 + c8) * N * 16, &wmap, (c8_0 + c8) * 8, t, ti.n0 * N, &full[st]);
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(N, 128);
+      int it = 0, tl = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tl) {
+        const int buf = tl & 1;
+        const unsigned ub = (unsigned)(tl >> 1);
+        if (tl >= 2 && !mbar_wait(&tempty[buf], (ub - 1u) & 1u, a.timeout_ns)) {
+          s_late = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t acc = tmem + (uint32_t)(buf * N);
+        for (int i = 0; i < nchunks; ++i, ++it) {
+          const int st = it % S;
+          const unsigned u = (unsigned)(it / S);
+          if (!mbar_wait(&full[st], u & 1u, a.timeout_ns)) {
+            s_late = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+          const unsigned abase = saddr(sm + st * SS), bbase = abase + SA;
+          for (int t = 0; t < 9; ++t) {
+            const int ky = t / 3, kx = t % 3;
+            const unsigned aaddr = abase + (kx * 2) * kPlaneBytes + ky * (kTW * 16);
+            const unsigned baddr = bbase + (unsigned)(t * 2 * N * 16);
+            mma_bf16(acc, smem_desc(aaddr, kPlaneBytes, 128), smem_desc(baddr, N * 16, 128), idesc,
+                     (i > 0 || t > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[st]);
+        }
+        if (ok) mma_commit(&tfull[buf]);
+      }
+      mma_commit(done);  // tracks every MMA issued above
+    }
+  } else {
+    // epilogue warps 0-3
+    int tl = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+      const int buf = tl & 1;
+      const unsigned ub = (unsigned)(tl >> 1);
+      if (!mbar_wait(&tfull[buf], ub & 1u, a.timeout_ns) || *(volatile int *)&s_late) {
+        s_late = 1;
+        break;
+      }
+      fence_after();
+      const TileIdx ti = tile_of(tile, tiles_x, tiles_pix, ntn);
+      const int n0 = ti.n0 * N;
+      const int m = warp * 32 + lane, gy = ti.ty0 + m / kTW, gx = ti.tx0 + m % kTW;
+      const bool in = gy < a.H && gx < a.W;
+      const long long obase = (((long long)ti.b * a.H + gy) * a.W + gx) * a.Cout + n0;
+#pragma unroll
+      for (int cb = 0; cb < N; cb += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * N + cb), r);
+        if (in) {
+          float v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            v[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[n0 + cb + j] : 0.0f);
+            if (a.relu) v[j] = fmaxf(v[j], 0.0f);
+          }
+          uint4 pk[2];
+          __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+          uint4 *dst = reinterpret_cast<uint4 *>(a.y + obase + cb);
+          dst[0] = pk[0];
+          dst[1] = pk[1];
+          if (a.y32) {
+            float4 *d32 = reinterpret_cast<float4 *>(a.y32 + obase + cb);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) d32[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          }
+        }
+      }
+      // this warp's reads of the accumulator are done: release it
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+  }
+  __syncthreads();
+  if (s_late) {
+    if (tid == 0) {
+      set_error(a.st, RF_ERR_TIMEOUT);
+      mbar_wait(done, 0u, a.timeout_ns);  // the issued MMAs, before TMEM is freed
+    }
+  } else if (tid == 0) {
+    mbar_wait(done, 0u, a.timeout_ns);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
 // Tensor maps.  x: dims (Cin, W, H, B) of the NHWC input, box (8, 16, 10, 1)
 // = one A plane [row][col][8 ch]; w: dims (Cin, 9, Cout) of the weights
 // [Cout][9][Cin], box (8, 1, N) = one B plane [n][8 ch].
@@ -463,10 +676,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 template <int N>
-rf_status launch_tma(const TcArgs &t, cudaStream_t s) {
+rf_status encode_maps(const TcArgs &t, CUtensorMap &xmap, CUtensorMap &wmap) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return RF_ERR_UNSUPPORTED;
-  alignas(64) CUtensorMap xmap, wmap;
   const cuuint64_t xdim[4] = {(cuuint64_t)t.Cin, (cuuint64_t)t.W, (cuuint64_t)t.H, (cuuint64_t)t.B};
   const cuuint64_t xstr[3] = {(cuuint64_t)t.Cin * 2, (cuuint64_t)t.W * t.Cin * 2, (cuuint64_t)t.H * t.W * t.Cin * 2};
   const cuuint32_t xbox[4] = {8, kTW, kPH, 1};
@@ -483,6 +695,10 @@ rf_status launch_tma(const TcArgs &t, cudaStream_t s) {
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return RF_ERR_UNSUPPORTED;
+  return RF_OK;
+}
+
+inline TmaArgs tma_args(const TcArgs &t) {
   TmaArgs a;
   a.bias = t.bias;
   a.y = t.y;
@@ -495,6 +711,15 @@ rf_status launch_tma(const TcArgs &t, cudaStream_t s) {
   a.relu = t.relu;
   a.st = t.st;
   a.timeout_ns = t.timeout_ns;
+  return a;
+}
+
+template <int N>
+rf_status launch_tma(const TcArgs &t, cudaStream_t s) {
+  alignas(64) CUtensorMap xmap, wmap;
+  rf_status rs = encode_maps<N>(t, xmap, wmap);
+  if (rs != RF_OK) return rs;
+  const TmaArgs a = tma_args(t);
   const size_t smem = tma_smem_bytes(N);
   if (cudaFuncSetAttribute(conv3x3_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
@@ -502,6 +727,24 @@ rf_status launch_tma(const TcArgs &t, cudaStream_t s) {
   const int tiles = ((t.W + kTW - 1) / kTW) * ((t.H + kTH - 1) / kTH);
   dim3 grid(tiles, (t.Cout + N - 1) / N, t.B);
   conv3x3_tma_kernel<N><<<grid, kThreads, smem, s>>>(xmap, wmap, a);
+  return cuda_status(cudaGetLastError());
+}
+
+// The persistent kernel: one CTA per SM (at most one per tile).
+template <int N>
+rf_status launch_persist(const TcArgs &t, int num_sms, cudaStream_t s) {
+  alignas(64) CUtensorMap xmap, wmap;
+  rf_status rs = encode_maps<N>(t, xmap, wmap);
+  if (rs != RF_OK) return rs;
+  const TmaArgs a = tma_args(t);
+  const size_t smem = persist_smem_bytes(N);
+  if (cudaFuncSetAttribute(conv3x3_persist_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return RF_ERR_CUDA;
+  const long long ntiles = (long long)((t.W + kTW - 1) / kTW) * ((t.H + kTH - 1) / kTH) * (t.Cout / N) * t.B;
+  if (ntiles > (1LL << 30)) return RF_ERR_INVALID_ARG;
+  const int grid = (int)std::min<long long>(ntiles, num_sms);
+  conv3x3_persist_kernel<N><<<grid, kPersistThreads, smem, s>>>(xmap, wmap, a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -551,6 +794,11 @@ extern "C" rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, i
   // the pipelined tensor-copy kernel; the plain one if a tensor map cannot
   // be encoded here
   rf_status rs = RF_ERR_UNSUPPORTED;
+  if (Cout % 128 == 0) rs = tc::launch_persist<128>(a, ctx->num_sms, s);
+  else if (Cout % 64 == 0) rs = tc::launch_persist<64>(a, ctx->num_sms, s);
+  else if (Cout % 32 == 0) rs = tc::launch_persist<32>(a, ctx->num_sms, s);
+  else rs = tc::launch_persist<16>(a, ctx->num_sms, s);
+  if (rs != RF_ERR_UNSUPPORTED) return rs;
   if (Cout % 128 == 0) rs = tc::launch_tma<128>(a, s);
   else if (Cout % 64 == 0) rs = tc::launch_tma<64>(a, s);
   else if (Cout % 32 == 0) rs = tc::launch_tma<32>(a, s);

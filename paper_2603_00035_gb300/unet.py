@@ -41,11 +41,14 @@ def _chk(st, where):
 
 
 def conv3x3(lib, h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s):
-    """rf_unet_conv3x3 on the tcgen05 kernel (tensor-memory accumulator, tensor
-    copies) where it measured faster on GB300 -- 128 or more output channels
-    (288-361 vs 236-256 TFLOP/s) -- and on the mma.sync kernel for the narrow
-    layers (176-223 vs 57-192 TFLOP/s at 32-64 output channels)."""
-    fn = lib.rf_unet_conv3x3_tc if Cout % 128 == 0 else lib.rf_unet_conv3x3
+    """rf_unet_conv3x3 on the tcgen05 kernel (persistent, tensor-memory
+    accumulators, tensor copies) where it measured faster on GB300 -- 128 or
+    more output channels (320-350 vs 236-247 TFLOP/s), and 64 -> 64 (217 vs
+    185) -- and on the mma.sync kernel for the narrow layers with few input
+    channels (157-197 vs 77-112 TFLOP/s at 16-32 input or 32 output
+    channels)."""
+    wide = Cout % 128 == 0 or (Cout % 64 == 0 and Cin >= 64)
+    fn = lib.rf_unet_conv3x3_tc if wide else lib.rf_unet_conv3x3
     return fn(h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s)
 
 
