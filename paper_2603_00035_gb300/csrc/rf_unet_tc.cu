@@ -463,13 +463,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Every wait is bounded by the context timeout; a timeout records
 // RF_ERR_TIMEOUT, every role leaves its loop, and the CTA waits (bounded)
 // for the MMAs it issued before freeing TMEM.
-__host__ __device__ constexpr int persist_stages(int N) {
-  return (int)((210u * 1024u) / (stage_a_bytes() + stage_b_bytes(N))) > 8
+// P output tiles (8 x 16 pixels each) stacked vertically form one unit of
+// the persistent kernel: they share each weight stage and one halo patch of
+// 8P + 2 rows.
+__host__ __device__ constexpr unsigned plane_bytes_p(int P) { return (unsigned)(kTH * P + 2) * kTW * 16; }
+__host__ __device__ constexpr unsigned stage_a_bytes_p(int P) { return 3u * 2u * plane_bytes_p(P); }
+__host__ __device__ constexpr int persist_stages(int N, int P) {
+  return (int)((210u * 1024u) / (stage_a_bytes_p(P) + stage_b_bytes(N))) > 8
              ? 8
-             : (int)((210u * 1024u) / (stage_a_bytes() + stage_b_bytes(N)));
+             : (int)((210u * 1024u) / (stage_a_bytes_p(P) + stage_b_bytes(N)));
 }
-__host__ __device__ constexpr size_t persist_smem_bytes(int N) {
-  return (size_t)persist_stages(N) * (stage_a_bytes() + stage_b_bytes(N)) + (2 * persist_stages(N) + 5) * 8 + 16;
+__host__ __device__ constexpr size_t persist_smem_bytes(int N, int P) {
+  return (size_t)persist_stages(N, P) * (stage_a_bytes_p(P) + stage_b_bytes(N)) + (2 * persist_stages(N, P) + 5) * 8 +
+         16;
 }
 constexpr int kPersistThreads = 192;
 
@@ -478,26 +484,44 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *m) {
 }
 
 struct TileIdx {
-  int tx0, ty0, n0, b;
+  int tx0, ty0, nt, b;
 };
-__device__ __forceinline__ TileIdx tile_of(int tile, int tiles_x, int tiles_pix, int ntn) {
+__device__ __forceinline__ TileIdx tile_of(int tile, int tiles_x, int tiles_pix, int ntn, int rows) {
   TileIdx r;
   const int pt = tile % tiles_pix, q = tile / tiles_pix;
-  r.n0 = (q % ntn);
+  r.nt = q % ntn;
   r.b = q / ntn;
   r.tx0 = (pt % tiles_x) * kTW;
-  r.ty0 = (pt / tiles_x) * kTH;
+  r.ty0 = (pt / tiles_x) * rows;
   return r;
 }
 
-template <int N>
+// Persistent form: one CTA per SM walks the units (P stacked 8 x 16 pixel
+// tiles x N channels; consecutive units share their weights), with two sets
+// of P accumulators in tensor memory so that a unit's epilogue overlaps the
+// next unit's MMAs.
+//  * warp 4 (producer): stage after stage, across units, as in
+//    conv3x3_tma_kernel (16 input channels per stage; the activation box
+//    is 8P + 2 rows high);
+//  * warp 5, lane 0 (MMA issuer): per unit, waits until the epilogue has
+//    released the unit's accumulator set, issues 9 P MMAs per stage (each
+//    weight stage serves the P tiles), commits each stage to its "empty"
+//    barrier and the unit to the set's "full" barrier;
+//  * warps 0-3 (epilogue; warp w reads TMEM lanes 32w .. 32w+31): wait for
+//    the set, add bias, ReLU, store, and release it (one arrival per warp).
+// Every wait is bounded by the context timeout; a timeout records
+// RF_ERR_TIMEOUT, every role leaves its loop, and the CTA waits (bounded)
+// for the MMAs it issued before freeing TMEM.
+template <int N, int P>
 __global__ void __launch_bounds__(kPersistThreads, 1)
     conv3x3_persist_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
                            TmaArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
-  constexpr int S = persist_stages(N);
-  constexpr unsigned kCols = (2 * N) < 32 ? 32 : 2 * N;
-  constexpr unsigned SA = stage_a_bytes(), SB = stage_b_bytes(N), SS = SA + SB;
+  constexpr int S = persist_stages(N, P);
+  constexpr unsigned kCols = (2 * P * N) < 32 ? 32 : 2 * P * N;
+  constexpr unsigned PB = plane_bytes_p(P);
+  constexpr unsigned SA = stage_a_bytes_p(P), SB = stage_b_bytes(N), SS = SA + SB;
+  static_assert(2 * P * N <= 512, "two accumulator sets fit in tensor memory");
   uint64_t *full = reinterpret_cast<uint64_t *>(sm + S * SS);
   uint64_t *empty = full + S;
   uint64_t *tfull = empty + S;  // [2]
@@ -507,7 +531,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
   __shared__ int s_late;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tiles_x = (a.W + kTW - 1) / kTW, tiles_pix = tiles_x * ((a.H + kTH - 1) / kTH);
+  constexpr int UR = kTH * P;  // pixel rows per unit
+  const int tiles_x = (a.W + kTW - 1) / kTW, tiles_pix = tiles_x * ((a.H + UR - 1) / UR);
   const int ntn = a.Cout / N, ntiles = tiles_pix * ntn * a.B;
   const int nchunks = a.Cin / 16;
 
@@ -534,7 +559,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     int it = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const TileIdx ti = tile_of(tile, tiles_x, tiles_pix, ntn);
+      const TileIdx ti = tile_of(tile, tiles_x, tiles_pix, ntn, UR);
       for (int i = 0; i < nchunks; ++i, ++it) {
         const int st = it % S;
         const unsigned u = (unsigned)(it / S);
@@ -552,11 +577,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         const int c8_0 = i * 2;
         if (lane < 6) {
           const int kx = lane >> 1, c8 = lane & 1;
-          tma_load_4d(sa + (kx * 2 + c8) * kPlaneBytes, &xmap, (c8_0 + c8) * 8, ti.tx0 + kx - 1, ti.ty0 - 1, ti.b,
-                      &full[st]);
+          tma_load_4d(sa + (kx * 2 + c8) * PB, &xmap, (c8_0 + c8) * 8, ti.tx0 + kx - 1, ti.ty0 - 1, ti.b, &full[st]);
         } else if (lane < 24) {
           const int j = lane - 6, t = j >> 1, c8 = j & 1;
-          tma_load_3d(sb + (t * 2 + c8) * N * 16, &wmap, (c8_0 + c8) * 8, t, ti.n0 * N, &full[st]);
+          tma_load_3d(sb + (t * 2 + c8) * N * 16, &wmap, (c8_0 + c8) * 8, t, ti.nt * N, &full[st]);
         }
       }
     }
@@ -573,7 +597,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
           break;
         }
         fence_after();
-        const uint32_t acc = tmem + (uint32_t)(buf * N);
         for (int i = 0; i < nchunks; ++i, ++it) {
           const int st = it % S;
           const unsigned u = (unsigned)(it / S);
@@ -586,10 +609,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
           const unsigned abase = saddr(sm + st * SS), bbase = abase + SA;
           for (int t = 0; t < 9; ++t) {
             const int ky = t / 3, kx = t % 3;
-            const unsigned aaddr = abase + (kx * 2) * kPlaneBytes + ky * (kTW * 16);
-            const unsigned baddr = bbase + (unsigned)(t * 2 * N * 16);
-            mma_bf16(acc, smem_desc(aaddr, kPlaneBytes, 128), smem_desc(baddr, N * 16, 128), idesc,
-                     (i > 0 || t > 0) ? 1u : 0u);
+            const uint64_t bd = smem_desc(bbase + (unsigned)(t * 2 * N * 16), N * 16, 128);
+#pragma unroll
+            for (int h = 0; h < P; ++h) {
+              // tile h: rows 8h + ky .. of copy kx (planes (kx, c8 0 / 1), PB apart)
+              const unsigned aaddr = abase + (kx * 2) * PB + (kTH * h + ky) * (kTW * 16);
+              mma_bf16(tmem + (uint32_t)((buf * P + h) * N), smem_desc(aaddr, PB, 128), bd, idesc,
+                       (i > 0 || t > 0) ? 1u : 0u);
+            }
           }
           mma_commit(&empty[st]);
         }
@@ -608,37 +635,41 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         break;
       }
       fence_after();
-      const TileIdx ti = tile_of(tile, tiles_x, tiles_pix, ntn);
-      const int n0 = ti.n0 * N;
-      const int m = warp * 32 + lane, gy = ti.ty0 + m / kTW, gx = ti.tx0 + m % kTW;
-      const bool in = gy < a.H && gx < a.W;
-      const long long obase = (((long long)ti.b * a.H + gy) * a.W + gx) * a.Cout + n0;
+      const TileIdx ti = tile_of(tile, tiles_x, tiles_pix, ntn, UR);
+      const int n0 = ti.nt * N;
+      const int m = warp * 32 + lane;
+#pragma unroll 1
+      for (int h = 0; h < P; ++h) {
+        const int gy = ti.ty0 + kTH * h + m / kTW, gx = ti.tx0 + m % kTW;
+        const bool in = gy < a.H && gx < a.W;
+        const long long obase = (((long long)ti.b * a.H + gy) * a.W + gx) * a.Cout + n0;
 #pragma unroll
-      for (int cb = 0; cb < N; cb += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * N + cb), r);
-        if (in) {
-          float v[16];
+        for (int cb = 0; cb < N; cb += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((buf * P + h) * N + cb), r);
+          if (in) {
+            float v[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            v[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[n0 + cb + j] : 0.0f);
-            if (a.relu) v[j] = fmaxf(v[j], 0.0f);
-          }
-          uint4 pk[2];
-          __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(pk);
+            for (int j = 0; j < 16; ++j) {
+              v[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[n0 + cb + j] : 0.0f);
+              if (a.relu) v[j] = fmaxf(v[j], 0.0f);
+            }
+            uint4 pk[2];
+            __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(pk);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-          uint4 *dst = reinterpret_cast<uint4 *>(a.y + obase + cb);
-          dst[0] = pk[0];
-          dst[1] = pk[1];
-          if (a.y32) {
-            float4 *d32 = reinterpret_cast<float4 *>(a.y32 + obase + cb);
+            for (int j = 0; j < 8; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            uint4 *dst = reinterpret_cast<uint4 *>(a.y + obase + cb);
+            dst[0] = pk[0];
+            dst[1] = pk[1];
+            if (a.y32) {
+              float4 *d32 = reinterpret_cast<float4 *>(a.y32 + obase + cb);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) d32[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+              for (int j = 0; j < 4; ++j) d32[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
           }
         }
       }
-      // this warp's reads of the accumulator are done: release it
+      // this warp's reads of the accumulator set are done: release it
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -676,12 +707,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 template <int N>
-rf_status encode_maps(const TcArgs &t, CUtensorMap &xmap, CUtensorMap &wmap) {
+rf_status encode_maps(const TcArgs &t, CUtensorMap &xmap, CUtensorMap &wmap, int box_rows = kPH) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return RF_ERR_UNSUPPORTED;
   const cuuint64_t xdim[4] = {(cuuint64_t)t.Cin, (cuuint64_t)t.W, (cuuint64_t)t.H, (cuuint64_t)t.B};
   const cuuint64_t xstr[3] = {(cuuint64_t)t.Cin * 2, (cuuint64_t)t.W * t.Cin * 2, (cuuint64_t)t.H * t.W * t.Cin * 2};
-  const cuuint32_t xbox[4] = {8, kTW, kPH, 1};
+  const cuuint32_t xbox[4] = {8, kTW, (cuuint32_t)box_rows, 1};
   const cuuint32_t one4[4] = {1, 1, 1, 1};
   if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)t.x, xdim, xstr, xbox, one4,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -730,21 +761,22 @@ rf_status launch_tma(const TcArgs &t, cudaStream_t s) {
   return cuda_status(cudaGetLastError());
 }
 
-// The persistent kernel: one CTA per SM (at most one per tile).
-template <int N>
+// The persistent kernel: one CTA per SM (at most one per unit of P tiles).
+template <int N, int P>
 rf_status launch_persist(const TcArgs &t, int num_sms, cudaStream_t s) {
   alignas(64) CUtensorMap xmap, wmap;
-  rf_status rs = encode_maps<N>(t, xmap, wmap);
+  rf_status rs = encode_maps<N>(t, xmap, wmap, kTH * P + 2);
   if (rs != RF_OK) return rs;
   const TmaArgs a = tma_args(t);
-  const size_t smem = persist_smem_bytes(N);
-  if (cudaFuncSetAttribute(conv3x3_persist_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  const size_t smem = persist_smem_bytes(N, P);
+  if (cudaFuncSetAttribute(conv3x3_persist_kernel<N, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return RF_ERR_CUDA;
-  const long long ntiles = (long long)((t.W + kTW - 1) / kTW) * ((t.H + kTH - 1) / kTH) * (t.Cout / N) * t.B;
+  const long long ntiles =
+      (long long)((t.W + kTW - 1) / kTW) * ((t.H + kTH * P - 1) / (kTH * P)) * (t.Cout / N) * t.B;
   if (ntiles > (1LL << 30)) return RF_ERR_INVALID_ARG;
   const int grid = (int)std::min<long long>(ntiles, num_sms);
-  conv3x3_persist_kernel<N><<<grid, kPersistThreads, smem, s>>>(xmap, wmap, a);
+  conv3x3_persist_kernel<N, P><<<grid, kPersistThreads, smem, s>>>(xmap, wmap, a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -794,10 +826,12 @@ extern "C" rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, i
   // the pipelined tensor-copy kernel; the plain one if a tensor map cannot
   // be encoded here
   rf_status rs = RF_ERR_UNSUPPORTED;
-  if (Cout % 128 == 0) rs = tc::launch_persist<128>(a, ctx->num_sms, s);
-  else if (Cout % 64 == 0) rs = tc::launch_persist<64>(a, ctx->num_sms, s);
-  else if (Cout % 32 == 0) rs = tc::launch_persist<32>(a, ctx->num_sms, s);
-  else rs = tc::launch_persist<16>(a, ctx->num_sms, s);
+  // 8 x 16 tiles per weight stage: as many as two accumulator sets leave
+  // room for in tensor memory (2 P N <= 512 columns)
+  if (Cout % 128 == 0) rs = tc::launch_persist<128, 2>(a, ctx->num_sms, s);
+  else if (Cout % 64 == 0) rs = tc::launch_persist<64, 4>(a, ctx->num_sms, s);
+  else if (Cout % 32 == 0) rs = tc::launch_persist<32, 4>(a, ctx->num_sms, s);
+  else rs = tc::launch_persist<16, 4>(a, ctx->num_sms, s);
   if (rs != RF_ERR_UNSUPPORTED) return rs;
   if (Cout % 128 == 0) rs = tc::launch_tma<128>(a, s);
   else if (Cout % 64 == 0) rs = tc::launch_tma<64>(a, s);

@@ -41,14 +41,13 @@ def _chk(st, where):
 
 
 def conv3x3(lib, h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s):
-    """rf_unet_conv3x3 on the tcgen05 kernel (persistent, tensor-memory
-    accumulators, tensor copies) where it measured faster on GB300 -- 128 or
-    more output channels (320-350 vs 236-247 TFLOP/s), and 64 -> 64 (217 vs
-    185) -- and on the mma.sync kernel for the narrow layers with few input
-    channels (157-197 vs 77-112 TFLOP/s at 16-32 input or 32 output
-    channels)."""
-    wide = Cout % 128 == 0 or (Cout % 64 == 0 and Cin >= 64)
-    fn = lib.rf_unet_conv3x3_tc if wide else lib.rf_unet_conv3x3
+    """rf_unet_conv3x3 on the tcgen05 kernel (persistent, tensor copies,
+    2-4 pixel tiles sharing each weight stage, two tensor-memory accumulator
+    sets) when both channel counts are at least 32 -- measured on GB300 at
+    446-470 vs 236-248 TFLOP/s (128+ output channels), 268 vs 187 (64 -> 64),
+    174-200 vs 169-196 (32 -> 32 / 64) -- and on the mma.sync kernel for the
+    16-channel layers (159 vs 144 TFLOP/s at 16 -> 32)."""
+    fn = lib.rf_unet_conv3x3_tc if (Cin >= 32 and Cout >= 32) else lib.rf_unet_conv3x3
     return fn(h, x, B, H, W, Cin, w, bias, Cout, relu, y, y32, s)
 
 
