@@ -353,6 +353,28 @@ rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src,
                      const float *T, const rf_record *rec, const float *dLdT,
                      float *dLdproj5, float *lambda, int algo, void *stream);
 
+/* ---- whole steps on host buffers --------------------------------------------
+ * Sec. 3 end to end for the inverse problem (a1 projection, a2-a4 forward
+ * solve, a5 record, a6-a8 adjoint, a9 projection backward), input and
+ * output in host memory.  For each step i < n_steps: raw5_h[i] (5 planes
+ * [ny*nx] FP32: L11, L21, L22, wx, wy before projection), src_h[i]
+ * ([ny*nx] uint8) and dLdT_h[i] ([ny*nx] FP32) are copied to the device;
+ * the step projects (eps, delta), solves (opts, NULL for defaults),
+ * records, solves the adjoint (algo: enum rf_adjoint_algo) and projects
+ * back; T_h[i] ([ny*nx]) and dLdraw_h[i] ([5*ny*nx], dL/draw5) receive the
+ * results.  Steps are pipelined: step i + 1's input copy and step i - 1's
+ * output copy run on the context's two copy streams while step i computes
+ * on `stream` (two device buffer sets, allocated on first use and kept by
+ * the context).  Host buffers should be page-locked for the copies to
+ * overlap.  Returns when every result has arrived; device errors of the
+ * solves are in the context statistics (rf_ctx_last_stats). */
+rf_status rf_step_host(rf_ctx *ctx, const rf_grid *grid, int n_steps,
+                       const float *const *raw5_h,
+                       const uint8_t *const *src_h,
+                       const float *const *dLdT_h, float eps, float delta,
+                       const rf_opts *opts, int algo, float *const *T_h,
+                       float *const *dLdraw_h, void *stream);
+
 /* ---- soft-min relaxation of the stencil selection --------------------------
  * Paper: Sec. 3.3 "Stencil Boundaries and Non-Smoothness" names soft-min
  * relaxations as an alternative to the hard minimum, without a formula.

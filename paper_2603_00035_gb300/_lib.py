@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "rf_unet_conv3x3_tc": [P, P, I, I, I, I, P, P, I, I, P, P, P],
         "rf_unet_conv3x3_wgrad": [P, P, P, I, I, I, I, I, P, P],
         "rf_unet_conv3x3_wgrad_tc": [P, P, P, I, I, I, I, I, P, P],
+        "rf_step_host": [P, ctypes.POINTER(Grid), I, P, P, P, F, F, ctypes.POINTER(Opts), I, P, P, P],
         "rf_unet_bias_grad": [P, P, I64, I, P, P],
         "rf_unet_flip_weights": [P, P, I, I, P, P],
         "rf_unet_maxpool2": [P, P, I, I, I, I, P, P, P],

@@ -275,6 +275,32 @@ def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=Non
     return dLdproj5, lam_t
 
 
+def rf_step_host(raw5_h, src_h, dLdT_h, h, eps, delta, T_h, dLdraw_h, opts=None, algo="ordered", ctx=None,
+                 stream=None, device=0):
+    """Whole steps (project, solve, record, adjoint, project back) on host
+    tensors, pipelined across steps inside the library: lists of CPU tensors
+    (preferably pinned) raw5_h [5, ny, nx] float32, src_h [ny, nx] uint8,
+    dLdT_h [ny, nx] float32, and outputs T_h [ny, nx], dLdraw_h [5, ny, nx]
+    float32, one entry per step.  Returns when the outputs are filled."""
+    nsteps = len(raw5_h)
+    if not (len(src_h) == len(dLdT_h) == len(T_h) == len(dLdraw_h) == nsteps):
+        raise ValueError("one input and output set per step")
+    _, ny, nx = raw5_h[0].shape if nsteps else (5, 1, 1)
+    for t, dt, shp in [(x, torch.float32, (5, ny, nx)) for x in raw5_h] + [(x, torch.uint8, (ny, nx)) for x in src_h] + \
+            [(x, torch.float32, (ny, nx)) for x in dLdT_h] + [(x, torch.float32, (ny, nx)) for x in T_h] + \
+            [(x, torch.float32, (5, ny, nx)) for x in dLdraw_h]:
+        if t.is_cuda or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
+            raise ValueError(f"host tensor {dt} {shp} contiguous expected, got {t.dtype} {tuple(t.shape)}")
+    ctx = ctx or Context.get(torch.device("cuda", device))
+    arr = lambda ts: (ctypes.c_void_p * max(1, nsteps))(*[t.data_ptr() for t in ts])
+    o = opts if opts is not None else make_opts()
+    a = {"sweep": L.RF_ADJ_SWEEP, "ordered": L.RF_ADJ_ORDERED, "levels": L.RF_ADJ_LEVELS}[algo]
+    g = _grid(ny, nx, h)
+    L.check(L.load().rf_step_host(ctx.handle, ctypes.byref(g), nsteps, arr(raw5_h), arr(src_h), arr(dLdT_h),
+                                  float(eps), float(delta), ctypes.byref(o), int(a), arr(T_h), arr(dLdraw_h),
+                                  _stream(stream)), "rf_step_host")
+
+
 # ---- soft-min relaxation (Sec. 3.3) -----------------------------------------------
 
 def rf_softmin_forward(proj5, eps, src, h, tau, opts=None, T=None, ctx=None, stream=None):

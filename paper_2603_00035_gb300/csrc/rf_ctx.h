@@ -36,6 +36,10 @@ struct rf_ctx {
   size_t tvbuf_cap = 0;
   unsigned char *tilebuf = nullptr;  // tile-queue solve: queue, tile states, halos
   size_t tilebuf_cap = 0;
+  unsigned char *stepbuf = nullptr;  // rf_step_host: two input/output sets and the intermediates
+  size_t stepbuf_cap = 0;
+  cudaStream_t step_in = nullptr, step_out = nullptr;  // rf_step_host: copy streams (created on first use)
+  cudaEvent_t step_ev[6] = {};                         // rf_step_host: in / done / out per set
 };
 
 namespace rf {
