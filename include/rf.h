@@ -117,7 +117,9 @@ typedef struct rf_opts {
   float window;       /* TILES: a round processes the queued tiles whose
                          key (smallest new boundary time that queued them)
                          is within window x (tile side) x (mean edge
-                         cost) of the smallest key (0 = auto: 2)           */
+                         cost) of the previous round's smallest key; the
+                         rest wait for a later round (0 = auto: 4 with
+                         16 x 16 tiles, 2 with 32 x 32)                    */
 } rf_opts;
 
 /* Per-node record of the converged forward solve (Alg. 2, first loop). */

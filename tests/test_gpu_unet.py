@@ -212,6 +212,52 @@ def test_unet_gradients_match_reference():
         assert rel(gb, grads[k][1]) < 0.15, (k, rel(gb, grads[k][1]))
 
 
+@pytest.mark.parametrize("B,H,W,seed", [(1, 32, 32, 3), (2, 16, 40, 4)])
+def test_unet_integer_network_bit_exact(B, H, W, seed):
+    """Whole network, bit for bit.  Weights in {-1, 0, 1} (about three
+    non-zeros per output channel and input position), integer biases, input
+    and output gradient: every stored activation and gradient is an integer
+    and every product and partial sum is an integer far below 2^24 (at most
+    a few 10^5 for these seeds, the weight-gradient sums over all pixels),
+    so FP32 accumulation in any order is exact, FP64 agrees, and both sides
+    round to BF16 identically (values above 256 do get rounded, to even
+    integers).  The forward output and every weight and bias gradient must
+    then equal the FP64 reference exactly: a wrong skip, concat split,
+    pooling route, upsample sum or ReLU mask anywhere in the composed
+    network shows as a mismatch, with no accumulation noise to hide it."""
+    net = UNet(cin=16, base=32, cout=16, seed=0)
+    rng = np.random.default_rng(seed)
+    params = {}
+    for step in net.plan:
+        if isinstance(step, tuple):
+            name, ci, co, relu = step
+            nz = rng.random((co, 3, 3, ci)) < 3.0 / (9 * ci)
+            w = np.where(nz, rng.choice([-1.0, 1.0], size=nz.shape), 0.0)
+            b = rng.integers(-1, 3, size=co).astype(np.float64) if relu else np.zeros(co)
+            net.W[name].copy_(torch.from_numpy(w.astype(np.float32)))
+            net.b[name].copy_(torch.from_numpy(b.astype(np.float32)))
+            params[name] = (w, b)
+    net.refresh()
+    x_t, x = bf16(rng.integers(-3, 4, size=(B, H, W, 16)))
+    out = net.forward(x_t)
+    ref, tape = U.unet_forward(params, x, net.plan, rnd=U.round_bf16)
+    # the kernel returns the last layer's FP32 sum, before any BF16 rounding
+    last = tape[-1]
+    assert last[0] == "conv" and last[1] == "out"
+    ref_out = U.conv3x3(last[2], params["out"][0], params["out"][1], False)
+    np.testing.assert_array_equal(out.cpu().numpy(), ref_out)
+    dy_t, dy = bf16(rng.integers(-2, 3, size=ref.shape))
+    net.zero_grad()
+    net.backward(dy_t)
+    grads = U.unet_backward(params, tape, dy, rnd=U.round_bf16)
+    for k in net.W:
+        gw, gb = grads[k]
+        # the case is not degenerate: gradient reaches every layer
+        assert (gw != 0).mean() > 0.02 and (gb != 0).any(), k
+        np.testing.assert_array_equal(net.gW[k].cpu().numpy(), gw, err_msg=k)
+        np.testing.assert_array_equal(net.gb[k].cpu().numpy(), gb, err_msg=k)
+
+
 def test_unet_training_reduces_loss():
     net = UNet(seed=2)
     opt = torch.optim.Adam(net.parameters(), lr=2e-3)
