@@ -43,11 +43,11 @@ TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_
                    "paper_2603_00035_gb300/csrc/rf_sweep_common.cuh", "paper_2603_00035_gb300/csrc/rf_device.cuh"]
 # kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
 # source check, then tile queue: plan, reset, seed, finish-seed, solve, stats; streamed: node records +
-# sweep; tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached -- CUB's sort kernels
-# not counted)
+# sweep; tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached; tiles: tile keys,
+# tile gather -- CUB's sort kernels not counted)
 LAUNCHES_BASE = 3
 LAUNCHES_FORWARD = {8: 8, 2: 4, 1: 3, 4: 3}
-LAUNCHES_ADJOINT = {"sweep": 1, "ordered": 3, "levels": 5}
+LAUNCHES_ADJOINT = {"sweep": 1, "ordered": 3, "levels": 5, "tiles": 2}
 
 
 def parse():
@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=2048)
-    p.add_argument("--algo", default="ordered", choices=["sweep", "ordered", "levels"])
+    p.add_argument("--algo", default="ordered", choices=["sweep", "ordered", "levels", "tiles"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 4, 8],
@@ -389,6 +389,10 @@ def run_ours(args):
         # levels: two sorts (2 x 16 B per node) + depth pass (id 1, T 4, order 4, state 8 r + 8 w, level 4)
         # + starts 4 + gather (order 4, id 1, w1 4, lambda 4 r + 4 w, g 4, dT 20, grad 20)
         bytes_per_launch = (32 + 29 + 4 + 65) * n * n
+    elif names[dom] == "adjoint" and args.algo == "tiles":
+        # tiles: tile keys (T 4 B per node; the tile sort is 16384 pairs) + per node id 1 + w1 4 + state
+        # 8 r + 8 w + g 4 + T 4 + dT 20 + grad 20
+        bytes_per_launch = (4 + 69) * n * n
     elif names[dom] == "adjoint":
         # ordered: sort keys+values (2 x 4 B in, 2 x 4 B out) + per node id 1 + w1 4 + state 8 r + 8 w
         # + g 4 + T 4 + dT 20 + grad 20

@@ -62,9 +62,12 @@ enum rf_mode {
 enum rf_adjoint_algo {
   RF_ADJ_SWEEP = 0,   /* transposed line sweeps until lambda stops changing */
   RF_ADJ_ORDERED = 1, /* radix sort on T, then dependency-ordered gather   */
-  RF_ADJ_LEVELS = 2   /* DAG-depth pass, radix sort on the level, then one
+  RF_ADJ_LEVELS = 2,  /* DAG-depth pass, radix sort on the level, then one
                          gather per level with a grid barrier between
                          levels; lambda equals RF_ADJ_ORDERED's bit for bit */
+  RF_ADJ_TILES = 3    /* 16 x 16 tiles taken by decreasing latest T, the
+                         chain inside a tile followed in shared memory;
+                         lambda equals RF_ADJ_ORDERED's bit for bit        */
 };
 
 /* Forward-solve kernel variants.  The first three run the paper's schedule
@@ -137,7 +140,8 @@ typedef struct rf_stats {
                            updates / nodes, rounded up)                   */
   int32_t converged;    /* 1 if the last sweep changed nothing            */
   int32_t adj_sweeps;   /* sweeps of the last adjoint (RF_ADJ_SWEEP), DAG
-                           levels of the last RF_ADJ_LEVELS adjoint       */
+                           levels of the last RF_ADJ_LEVELS adjoint, tiles
+                           that yielded in the last RF_ADJ_TILES adjoint */
   int64_t cell_updates; /* node updates of the last forward (line sweeps:
                            sweeps * ny * nx; TILES: nodes evaluated)      */
   float max_residual;   /* max |T - min valid candidate(T)| (record pass) */
@@ -159,6 +163,12 @@ rf_status rf_ctx_destroy(rf_ctx *ctx);
  * expires the kernel records RF_ERR_TIMEOUT, every CTA leaves its loops and
  * the launch ends; the context stays usable.  Default 2e9 (2 s). */
 rf_status rf_ctx_set_timeout(rf_ctx *ctx, int64_t timeout_ns);
+
+/* RF_ADJ_TILES: how long (ns, >= 0) a tile whose nodes wait for children
+ * held by other tiles may see no progress before it yields its CTA and is
+ * retried later (default 2000000).  A scheduling choice only: the results do
+ * not depend on it; 0 yields at every stall. */
+rf_status rf_ctx_set_adjoint_park(rf_ctx *ctx, int64_t park_ns);
 
 /* Synchronise the stream of the context's last call and copy the device
  * statistics (including the device status word) into *out (host memory).
@@ -347,8 +357,8 @@ rf_status rf_residual(rf_ctx *ctx, const rf_grid *grid, const float *proj5,
  * into dLdproj5 (5 planes, zero at sources and unreached nodes).
  * T, rec: from rf_sweep_forward; dLdT: [ny*nx] (ignored where T = +inf);
  * lambda (nullable): [ny*nx] output.  algo: enum rf_adjoint_algo.
- * RF_ADJ_ORDERED and RF_ADJ_LEVELS wait (bounded by the context's timeout)
- * for donors or children named by the record; a record whose donors do not
+ * RF_ADJ_ORDERED, RF_ADJ_LEVELS and RF_ADJ_TILES wait (bounded by the
+ * context's timeout) for donors or children named by the record; a record whose donors do not
  * have strictly smaller T ends in RF_ERR_TIMEOUT in the stats, with the
  * outputs incomplete.  Scratch: the context's buffers, grown as needed. */
 rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src,

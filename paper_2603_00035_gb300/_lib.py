@@ -19,7 +19,7 @@ RF_OK, RF_ERR_INVALID_ARG, RF_ERR_CUDA, RF_ERR_NOT_CONVERGED, RF_ERR_TIMEOUT = 0
 RF_ERR_NONFINITE_INPUT, RF_ERR_NO_SOURCE, RF_ERR_NO_MEMORY, RF_ERR_UNSUPPORTED = 5, 6, 7, 8
 RF_SWEEP_AUTO, RF_SWEEP_TILED1, RF_SWEEP_STREAMED, RF_SWEEP_TILED4, RF_SWEEP_TILES = 0, 1, 2, 4, 8
 RF_MODE_COLD, RF_MODE_WARM = 0, 1
-RF_ADJ_SWEEP, RF_ADJ_ORDERED, RF_ADJ_LEVELS = 0, 1, 2
+RF_ADJ_SWEEP, RF_ADJ_ORDERED, RF_ADJ_LEVELS, RF_ADJ_TILES = 0, 1, 2, 3
 
 
 class RFError(RuntimeError):
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
         "rf_ctx_create": [ctypes.POINTER(P), I],
         "rf_ctx_destroy": [P],
         "rf_ctx_set_timeout": [P, ctypes.c_int64],
+        "rf_ctx_set_adjoint_park": [P, ctypes.c_int64],
         "rf_ctx_last_stats": [P, ctypes.POINTER(Stats)],
         "rf_project": [P, ctypes.POINTER(Grid), P, F, F, P, P, P],
         "rf_project_backward": [P, ctypes.POINTER(Grid), P, P, F, F, P, P, P],

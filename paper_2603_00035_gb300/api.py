@@ -58,6 +58,10 @@ class Context:
     def set_timeout(self, ns: int):
         L.check(L.load().rf_ctx_set_timeout(self.handle, int(ns)), "rf_ctx_set_timeout")
 
+    def set_adjoint_park(self, ns: int):
+        """RF_ADJ_TILES: stall (ns) before a waiting tile yields its CTA."""
+        L.check(L.load().rf_ctx_set_adjoint_park(self.handle, int(ns)), "rf_ctx_set_adjoint_park")
+
     def raise_on_device_error(self, where: str):
         """Synchronise the last call's stream and raise RFError when the
         device status word holds an error (RF_ERR_NOT_CONVERGED,
@@ -199,6 +203,11 @@ def rf_tv(gb5, metric="frobenius", w_metric=1.0, w_drift=1.0, grad5=None, value=
 SWEEP_VARIANTS = {"auto": L.RF_SWEEP_AUTO, "tiled1": L.RF_SWEEP_TILED1, "streamed": L.RF_SWEEP_STREAMED,
                   "tiled4": L.RF_SWEEP_TILED4, "tiles": L.RF_SWEEP_TILES}
 
+# adjoint schedules (enum rf_adjoint_algo); "ordered", "levels" and "tiles"
+# give the same multipliers and gradients bit for bit
+ADJ_ALGOS = {"sweep": L.RF_ADJ_SWEEP, "ordered": L.RF_ADJ_ORDERED, "levels": L.RF_ADJ_LEVELS,
+             "tiles": L.RF_ADJ_TILES}
+
 
 def make_opts(tol=0.0, max_sweeps=64, warm=False, band=0, block=0, rtol=1e-6, variant=0, window=0.0):
     """rf_opts: a node counts as changed when |dT| > tol + rtol * T (tol =
@@ -259,7 +268,7 @@ def rf_residual(proj5, eps, src, h, T, per_node=False, ctx=None, stream=None):
 
 def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=None, stream=None):
     """a6-a8: solve J^T lambda = g on the recorded stencils and contract with
-    the partials.  algo: "sweep", "ordered" or "levels".  Returns (dL/d(L11,
+    the partials.  algo: a name of ADJ_ALGOS.  Returns (dL/d(L11,
     L21, L22, wx, wy) of the projected fields, lambda or None)."""
     ny, nx = T.shape
     _check_cuda(dLdT, torch.float32, (ny, nx), name="dLdT")
@@ -267,7 +276,7 @@ def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=Non
     dLdproj5 = dLdproj5 if dLdproj5 is not None else torch.empty((5, ny, nx), dtype=torch.float32,
                                                                  device=T.device)
     lam_t = torch.empty((ny, nx), dtype=torch.float32, device=T.device) if lam else None
-    a = {"sweep": L.RF_ADJ_SWEEP, "ordered": L.RF_ADJ_ORDERED, "levels": L.RF_ADJ_LEVELS}[algo]
+    a = ADJ_ALGOS[algo]
     g = _grid(ny, nx, 1.0)
     crec = rec.c()
     L.check(L.load().rf_adjoint(ctx.handle, ctypes.byref(g), _ptr(src), _ptr(T), ctypes.byref(crec),
@@ -294,7 +303,7 @@ def rf_step_host(raw5_h, src_h, dLdT_h, h, eps, delta, T_h, dLdraw_h, opts=None,
     ctx = ctx or Context.get(torch.device("cuda", device))
     arr = lambda ts: (ctypes.c_void_p * max(1, nsteps))(*[t.data_ptr() for t in ts])
     o = opts if opts is not None else make_opts()
-    a = {"sweep": L.RF_ADJ_SWEEP, "ordered": L.RF_ADJ_ORDERED, "levels": L.RF_ADJ_LEVELS}[algo]
+    a = ADJ_ALGOS[algo]
     g = _grid(ny, nx, h)
     L.check(L.load().rf_step_host(ctx.handle, ctypes.byref(g), nsteps, arr(raw5_h), arr(src_h), arr(dLdT_h),
                                   float(eps), float(delta), ctypes.byref(o), int(a), arr(T_h), arr(dLdraw_h),

@@ -3,12 +3,14 @@
 Each translation unit in csrc/ is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a -lineinfo -O3) and linked into
 paper_2603_00035_gb300/librf.so.  Rebuilds only when a source or header is
-newer than the library.
+newer than the library, and then recompiles only the translation units
+older than their source or a header.
 """
 from __future__ import annotations
 
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -17,7 +19,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+# objects per host architecture: a tree copied between machines never mixes them
+BUILD = os.path.join(HERE, "_build", platform.machine() or "host")
 LIB = os.path.join(HERE, "librf.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -52,8 +55,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     common = ["-std=c++17", "-O3", "-lineinfo", ARCH, "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
+    # an object is reused when it is newer than its source and every header
+    headers = max((os.path.getmtime(d) for d in _deps() if not d.endswith(".cu")), default=0.0)
+
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), headers):
+            return obj
         cmd = [nvcc] + common + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

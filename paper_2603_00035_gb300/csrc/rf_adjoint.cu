@@ -281,23 +281,6 @@ struct OrderedArgs {
   LaunchCtl ctl;
 };
 
-// Polling load: the child's multiplier and the epoch tag sit in one 64-bit
-// word written by one store, so a relaxed (single-copy atomic) load that
-// sees the tag sees the value; unlike an acquire load it does not hold back
-// the loads of the other children.
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-// Publishing store: a parent reads nothing of its child but this one 64-bit
-// word (multiplier and epoch tag together), so single-copy atomicity is all
-// the hand-over needs -- no release fence, which would first wait for the
-// thread's earlier gradient stores to reach L2.
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // Grid of packed node p: the last grid whose first node is <= p.
 __device__ __forceinline__ int grid_of(const TGrid *grids, int n_grids, long long p) {
   int lo = 0, hi = n_grids - 1;
@@ -649,9 +632,13 @@ namespace {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+}  // namespace
+
+namespace rf {
+
 // Next launch epoch for the tagged per-node state words (cleared on first
 // use and whenever the epoch counter wraps).
-rf_status next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, unsigned *epoch) {
+rf_status adjoint_next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, unsigned *epoch) {
   const bool fresh = ctx->adj_state_cap < (size_t)n || !ctx->adj_state;
   rf_status rs;
   if ((rs = ensure(&ctx->adj_state, &ctx->adj_state_cap, (size_t)n)) != RF_OK) return rs;
@@ -663,10 +650,6 @@ rf_status next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, unsigned *epoch) 
   *epoch = ++ctx->adj_epoch;
   return RF_OK;
 }
-
-}  // namespace
-
-namespace rf {
 
 // The ordered adjoint of one grid (grids == NULL: shape ny x nx) or of
 // packed grids (grids: device descriptors with increasing node offsets, n
@@ -690,7 +673,7 @@ rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid 
   unsigned *ctl_words = (unsigned *)(base + 4 * arr);  // [0] ticket, [1] abort
   void *temp = base + 4 * arr + 256;
   unsigned epoch;
-  if ((rs = next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
+  if ((rs = adjoint_next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
   if (cudaMemsetAsync(ctl_words, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return RF_ERR_CUDA;
 
   ordered_keys_kernel<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(T, kin, vin, n);
@@ -764,7 +747,7 @@ rf_status adjoint_levels(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const 
   void *temp = base + 4 * arr + arr1 + 256;
   if ((rs = ensure(&ctx->lbuf, &ctx->lbuf_cap, (size_t)n)) != RF_OK) return rs;
   unsigned epoch;
-  if ((rs = next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
+  if ((rs = adjoint_next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
   if (cudaMemsetAsync(ctl_words, 0, 6 * sizeof(unsigned), s) != cudaSuccess ||
       cudaMemsetAsync(&ctx->state->adj_sweeps, 0, sizeof(int), s) != cudaSuccess)
     return RF_ERR_CUDA;
@@ -831,8 +814,11 @@ extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t 
   if (!ctx || !grid_ok(grid) || !src || !T || !rec || !rec->id || !rec->w1 || !rec->dT || !dLdT ||
       !dLdproj5)
     return RF_ERR_INVALID_ARG;
-  if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED && algo != RF_ADJ_LEVELS) return RF_ERR_INVALID_ARG;
+  if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED && algo != RF_ADJ_LEVELS && algo != RF_ADJ_TILES)
+    return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
+  if (algo == RF_ADJ_TILES)
+    return rf::adjoint_tiles(ctx, grid->ny, grid->nx, src, T, rec, dLdT, dLdproj5, lambda, (cudaStream_t)stream);
   if (algo == RF_ADJ_LEVELS)
     return rf::adjoint_levels(ctx, grid->ny, grid->nx, src, T, rec, dLdT, dLdproj5, lambda, (cudaStream_t)stream);
   if (algo == RF_ADJ_ORDERED)

@@ -1,5 +1,6 @@
 // rf_adjoint.h -- internal interface of the ordered adjoint (rf_adjoint.cu),
-// used by rf_adjoint and by the tile-queue path of rf_batch_solve.
+// used by rf_adjoint and by the tile-queue path of rf_batch_solve, and of
+// the tiled adjoint (rf_adjoint_tiles.cu).
 #pragma once
 
 #include "rf_ctx.h"
@@ -15,5 +16,15 @@ struct TGrid;
 rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid *grids, int n_grids,
                           const uint8_t *src, const float *T, const rf_record *rec, const float *dLdT,
                           float *dLdproj5, float *lambda, cudaStream_t s);
+
+// Alg. 2 on one grid with the dependency chain followed inside 16 x 16
+// tiles in shared memory (RF_ADJ_TILES); same outputs as adjoint_ordered,
+// bit for bit.
+rf_status adjoint_tiles(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const float *T, const rf_record *rec,
+                        const float *dLdT, float *dLdproj5, float *lambda, cudaStream_t s);
+
+// Next epoch of the context's tagged per-node state words (n of them),
+// clearing them on first use and when the epoch counter wraps.
+rf_status adjoint_next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, unsigned *epoch);
 
 }  // namespace rf

@@ -55,6 +55,12 @@ extern "C" rf_status rf_ctx_set_timeout(rf_ctx *c, int64_t timeout_ns) {
   return RF_OK;
 }
 
+extern "C" rf_status rf_ctx_set_adjoint_park(rf_ctx *c, int64_t park_ns) {
+  if (!c || park_ns < 0) return RF_ERR_INVALID_ARG;
+  c->adj_park_ns = (long long)park_ns;
+  return RF_OK;
+}
+
 extern "C" rf_status rf_ctx_last_stats(rf_ctx *c, rf_stats *out) {
   if (!c || !out) return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return RF_ERR_CUDA;

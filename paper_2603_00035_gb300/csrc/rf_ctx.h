@@ -15,6 +15,7 @@ struct rf_ctx {
   cudaStream_t last_stream = nullptr;
   rf::DevState *state = nullptr;  // device status word and counters
   long long timeout_ns = 2000000000LL;  // bound of every device wait
+  long long adj_park_ns = 2000000;      // RF_ADJ_TILES: stall before a tile yields its CTA
 
   // grown on demand
   unsigned *progress = nullptr;  // per-band progress tokens

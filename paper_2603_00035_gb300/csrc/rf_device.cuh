@@ -186,6 +186,23 @@ __device__ __forceinline__ int ld_acquire_s32(const int *p) {
   return v;
 }
 
+// Polling load: the child's multiplier and the epoch tag sit in one 64-bit
+// word written by one store, so a relaxed (single-copy atomic) load that
+// sees the tag sees the value; unlike an acquire load it does not hold back
+// the loads of the other children.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+// Publishing store: a parent reads nothing of its child but this one 64-bit
+// word (multiplier and epoch tag together), so single-copy atomicity is all
+// the hand-over needs -- no release fence, which would first wait for the
+// thread's earlier gradient stores to reach L2.
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Device status word layout shared by the kernels (one per context).
 struct DevState {
   int status;          // rf_status

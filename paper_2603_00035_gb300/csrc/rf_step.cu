@@ -69,7 +69,8 @@ extern "C" rf_status rf_step_host(rf_ctx *ctx, const rf_grid *grid, int n_steps,
     return RF_ERR_INVALID_ARG;
   for (int i = 0; i < n_steps; ++i)
     if (!raw5_h[i] || !src_h[i] || !dLdT_h[i] || !T_h[i] || !dLdraw_h[i]) return RF_ERR_INVALID_ARG;
-  if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED && algo != RF_ADJ_LEVELS) return RF_ERR_INVALID_ARG;
+  if (algo != RF_ADJ_SWEEP && algo != RF_ADJ_ORDERED && algo != RF_ADJ_LEVELS && algo != RF_ADJ_TILES)
+    return RF_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return RF_ERR_CUDA;
   if (n_steps == 0) return RF_OK;
   cudaStream_t s = (cudaStream_t)stream;
