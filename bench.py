@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=2048)
-    p.add_argument("--algo", default="ordered", choices=["sweep", "ordered", "levels", "tiles"])
+    p.add_argument("--algo", default="tiles", choices=["sweep", "ordered", "levels", "tiles"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 4, 8],
@@ -500,7 +500,7 @@ def batch_measure(grids, steps, warmup, dev, world=1, sampler=None, variant=0):
         for raw, src, gg, h in per:
             proj, clip = api.rf_project(raw, 1e-6, 0.05)
             T, rec = api.rf_sweep_forward(proj, 1e-6, src, h)
-            gproj, _ = api.rf_adjoint(src, T, rec, gg, algo="ordered", lam=False)
+            gproj, _ = api.rf_adjoint(src, T, rec, gg, algo="tiles", lam=False)
             api.rf_project_backward(raw, clip, 1e-6, 0.05, gproj)
 
     plain()

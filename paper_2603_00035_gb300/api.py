@@ -284,7 +284,7 @@ def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=Non
     return dLdproj5, lam_t
 
 
-def rf_step_host(raw5_h, src_h, dLdT_h, h, eps, delta, T_h, dLdraw_h, opts=None, algo="ordered", ctx=None,
+def rf_step_host(raw5_h, src_h, dLdT_h, h, eps, delta, T_h, dLdraw_h, opts=None, algo="tiles", ctx=None,
                  stream=None, device=0):
     """Whole steps (project, solve, record, adjoint, project back) on host
     tensors, pipelined across steps inside the library: lists of CPU tensors

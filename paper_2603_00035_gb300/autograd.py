@@ -32,7 +32,7 @@ class RFSolve(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, raw5, src, h, eps=1e-6, delta=0.05, algo="ordered", opts=None):
+    def forward(ctx, raw5, src, h, eps=1e-6, delta=0.05, algo="tiles", opts=None):
         raw5 = raw5.contiguous()
         proj, clip = api.rf_project(raw5, eps, delta)
         T, rec = api.rf_sweep_forward(proj, eps, src, h, opts=opts)
@@ -53,7 +53,7 @@ class RFSolve(torch.autograd.Function):
         return graw, None, None, None, None, None, None
 
 
-def rf_solve(raw5, src, h, eps=1e-6, delta=0.05, algo="ordered", opts=None):
+def rf_solve(raw5, src, h, eps=1e-6, delta=0.05, algo="tiles", opts=None):
     """Differentiable arrival times T(raw5) (see RFSolve)."""
     return RFSolve.apply(raw5, src, h, eps, delta, algo, opts)
 
@@ -115,7 +115,7 @@ class SweepSolve(torch.autograd.Function):
     stencil-record adjoint (Alg. 2)."""
 
     @staticmethod
-    def forward(ctx, proj5, src, h, eps=1e-6, algo="ordered", opts=None):
+    def forward(ctx, proj5, src, h, eps=1e-6, algo="tiles", opts=None):
         proj5 = proj5.contiguous()
         T, rec = api.rf_sweep_forward(proj5, eps, src, h, opts=opts)
         api.Context.get(proj5.device).raise_on_device_error("SweepSolve.forward")
@@ -153,7 +153,7 @@ class TotalVariation(torch.autograd.Function):
         return grad * gout, None, None, None
 
 
-def metric_solve(gb5, src, h, prm, algo="ordered", opts=None):
+def metric_solve(gb5, src, h, prm, algo="tiles", opts=None):
     """Differentiable T of the paper's raw (g11, g12, g22, b1, b2) fields:
     App. B projection, then the solve.  Returns (T, gbp5)."""
     gbp5, proj5 = MetricProject.apply(gb5, prm)

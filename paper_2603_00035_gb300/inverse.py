@@ -30,7 +30,7 @@ def metric_from_raw(raw5, eps):
 
 
 def run_inverse(raw_true, src, obs, h, steps=200, eps=1e-6, delta=0.05, lr_metric=1e-2, lr_drift=5e-3,
-                algo="ordered", log_every=0):
+                algo="tiles", log_every=0):
     """raw_true: (5, ny, nx) float32 CUDA ground truth; src, obs: uint8 masks."""
     dev = raw_true.device
     with torch.no_grad():
@@ -74,7 +74,7 @@ def run_inverse(raw_true, src, obs, h, steps=200, eps=1e-6, delta=0.05, lr_metri
 
 
 def run_inverse_paper(gb_true, sources, obs, h, mode="iso", steps=300, init=1.5, tv_weight=1e-3,
-                      tv_metric="frobenius", prm=None, lr_metric=1e-2, lr_drift=5e-3, clip=1.0, algo="ordered",
+                      tv_metric="frobenius", prm=None, lr_metric=1e-2, lr_drift=5e-3, clip=1.0, algo="tiles",
                       opts=None, noise=0.0, seed=0):
     """The paper's synthetic inverse experiments (Eq. 8; App. "Inverse
     Problem Experiments") in its own parameterisation (G, b):
@@ -220,7 +220,7 @@ def main():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--obs", type=float, default=0.005)
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--algo", default="ordered")
+    p.add_argument("--algo", default="tiles")
     p.add_argument("--paper", action="store_true",
                    help="run the paper's 80x80 synthetic recoveries in its (G, b) parameterisation")
     a = p.parse_args()
