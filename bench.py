@@ -516,7 +516,7 @@ def batch_measure(grids, steps, warmup, dev, world=1, sampler=None, variant=0):
             "how": "one CUDA-graph replay of rf_project + rf_batch_solve + rf_project_backward (variant, tile side "
                    "and window from the batch autotuner unless given)",
             "plain_form": {"value": plain_rate, "unit": UNIT, "ms_per_batch": plain_ms,
-                           "how": "rf_project, rf_sweep_forward, rf_adjoint(ordered), rf_project_backward per grid"},
+                           "how": "rf_project, rf_sweep_forward, rf_adjoint (tiles), rf_project_backward per grid"},
             "speedup_vs_plain": rate / plain_rate,
             "autotuned": None if tuned is None else {"band": tuned[0], "variant": tuned[1], "window": tuned[2]}}
 
