@@ -89,7 +89,9 @@ def run_inverse_paper(gb_true, sources, obs, h, mode="iso", steps=300, init=1.5,
     gradient descent).
 
     mode "iso": G = g I with g free (b fixed to the truth); "drift": b free
-    (G fixed to the truth); "full": all five fields free.  gb_true: float32
+    per node (G fixed to the truth); "drift_const": one constant drift
+    vector b free (G fixed to the truth; the appendix's constant-drift
+    example read as a two-parameter problem); "full": all five fields free.  gb_true: float32
     CUDA (5, ny, nx); sources: list of uint8 (ny, nx) masks; obs: list of
     uint8 masks (one per source); noise: Gaussian noise added to the observed
     times, as a fraction of their standard deviation.  Returns the loss
@@ -116,6 +118,10 @@ def run_inverse_paper(gb_true, sources, obs, h, mode="iso", steps=300, init=1.5,
         params = [torch.nn.Parameter(torch.full((2, ny, nx), float(init), device=dev))]
         groups = [{"params": params, "lr": lr_drift}]
         assemble = lambda: torch.cat([gb_true[:3], params[0]])
+    elif mode == "drift_const":
+        params = [torch.nn.Parameter(torch.full((2,), float(init), device=dev))]
+        groups = [{"params": params, "lr": lr_drift}]
+        assemble = lambda: torch.cat([gb_true[:3], params[0].view(2, 1, 1).expand(2, ny, nx)])
     elif mode == "full":
         g0 = torch.stack([torch.full((ny, nx), float(init), device=dev), z, torch.full((ny, nx), float(init),
                                                                                     device=dev)])
@@ -150,6 +156,8 @@ def run_inverse_paper(gb_true, sources, obs, h, mode="iso", steps=300, init=1.5,
                 params[0].copy_(gbp_new[0])
             elif mode == "drift":
                 params[0].copy_(gbp_new[3:])
+            elif mode == "drift_const":
+                params[0].copy_(gbp_new[3:].mean(dim=(1, 2)))
             else:
                 params[0].copy_(gbp_new[:3])
                 params[1].copy_(gbp_new[3:])
@@ -165,7 +173,7 @@ def run_inverse_paper(gb_true, sources, obs, h, mode="iso", steps=300, init=1.5,
                    ms_per_iteration=1e3 * elapsed / steps)
         if mode in ("iso", "full"):
             out["rel_err_metric"] = rel(gb[:3], gb_true[:3])
-        if mode in ("drift", "full"):
+        if mode in ("drift", "drift_const", "full"):
             out["rel_err_b1"] = rel(gb[3], gb_true[3])
             out["rel_err_b2"] = rel(gb[4], gb_true[4])
             for c in (3, 4):
@@ -198,6 +206,8 @@ def paper_experiments(steps=300, seed=0, device="cuda"):
     for w in (1e-3, 1e-2, 1e-1):
         yield dict(run=f"drift_full_obs_tv{w:g}", **run_inverse_paper(drift, centre, full, h, "drift", steps, init=0.0,
                                                                      tv_weight=w))
+    yield dict(run="drift_constant_full_obs", **run_inverse_paper(drift, centre, full, h, "drift_const", steps,
+                                                                  init=0.0, tv_weight=0.0))
     for k in (1, 2, 3, 5):
         srcs = [t(m) for m in (R.random_sources(n, n, 1, seed + 101 * i, margin=8) for i in range(k))]
         yield dict(run=f"multisource_{k}", **run_inverse_paper(iso, srcs, sparse(k), h, "iso", steps))
