@@ -274,7 +274,7 @@ struct OrderedArgs {
   const float *g;
   const unsigned *order;  // node indices by decreasing T
   unsigned long long *state;  // (epoch << 32) | lambda bits
-  unsigned epoch;
+  const unsigned *epoch;      // this launch's tag (device word, bumped before the launch)
   unsigned *ticket;
   float *grad;
   float *lam_out;
@@ -295,7 +295,7 @@ __device__ __forceinline__ int grid_of(const TGrid *grids, int n_grids, long lon
 __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
   const int lane = threadIdx.x & 31;
   const long long n = a.n;
-  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  const unsigned long long tag = (unsigned long long)__ldg(a.epoch) << 32;
   while (true) {
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(a.ticket, 32u);
@@ -415,7 +415,7 @@ struct LevelArgs {
   const float *g;
   const unsigned *order;      // depth pass: node indices by decreasing T
   unsigned long long *state;  // depth pass: (epoch << 32) | level
-  unsigned epoch;
+  const unsigned *epoch;      // this launch's tag (device word, bumped before the launch)
   unsigned *ticket;
   unsigned *level;            // depth pass output: level of each node (n for unreached nodes)
   unsigned *n_levels;         // depth pass: 1 + the largest level (0: no reached node)
@@ -435,7 +435,7 @@ __device__ __forceinline__ bool in_grid(int i, int j, int ny, int nx) {
 __global__ void __launch_bounds__(256) level_depth_kernel(LevelArgs a) {
   const int lane = threadIdx.x & 31;
   const long long n = a.n;
-  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  const unsigned long long tag = (unsigned long long)__ldg(a.epoch) << 32;
   unsigned wmax = 0;
   while (true) {
     unsigned base = 0;
@@ -636,19 +636,30 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 namespace rf {
 
-// Next launch epoch for the tagged per-node state words (cleared on first
-// use and whenever the epoch counter wraps).
-rf_status adjoint_next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, unsigned *epoch) {
+// The epoch tagging the per-node state words lives on the device and is
+// bumped by a kernel on the launch stream, so a replayed CUDA graph gets a
+// new tag on every replay (a tag fixed at capture would find every word
+// already final from the previous replay).  The words are cleared on first
+// use and when the host's count of launches nears the 32-bit wrap.
+__global__ void epoch_bump_kernel(unsigned *e) {
+  const unsigned v = *e + 1u;
+  *e = v ? v : 1u;
+}
+
+rf_status adjoint_next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, const unsigned **epoch) {
   const bool fresh = ctx->adj_state_cap < (size_t)n || !ctx->adj_state;
   rf_status rs;
   if ((rs = ensure(&ctx->adj_state, &ctx->adj_state_cap, (size_t)n)) != RF_OK) return rs;
-  if (fresh || ctx->adj_epoch == 0xffffffffu) {
-    if (cudaMemsetAsync(ctx->adj_state, 0, sizeof(unsigned long long) * ctx->adj_state_cap, s) != cudaSuccess)
+  if (fresh || ctx->adj_epoch == 0xfffffff0u) {
+    if (cudaMemsetAsync(ctx->adj_state, 0, sizeof(unsigned long long) * ctx->adj_state_cap, s) != cudaSuccess ||
+        cudaMemsetAsync(&ctx->state->adj_epoch, 0, sizeof(unsigned), s) != cudaSuccess)
       return RF_ERR_CUDA;
     ctx->adj_epoch = 0;
   }
-  *epoch = ++ctx->adj_epoch;
-  return RF_OK;
+  ++ctx->adj_epoch;
+  epoch_bump_kernel<<<1, 1, 0, s>>>(&ctx->state->adj_epoch);
+  *epoch = &ctx->state->adj_epoch;
+  return cuda_status(cudaGetLastError());
 }
 
 // The ordered adjoint of one grid (grids == NULL: shape ny x nx) or of
@@ -672,7 +683,7 @@ rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid 
            *vout = (unsigned *)(base + 3 * arr);
   unsigned *ctl_words = (unsigned *)(base + 4 * arr);  // [0] ticket, [1] abort
   void *temp = base + 4 * arr + 256;
-  unsigned epoch;
+  const unsigned *epoch;
   if ((rs = adjoint_next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
   if (cudaMemsetAsync(ctl_words, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return RF_ERR_CUDA;
 
@@ -746,7 +757,7 @@ rf_status adjoint_levels(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const 
   unsigned *ctl_words = (unsigned *)(base + 4 * arr + arr1);
   void *temp = base + 4 * arr + arr1 + 256;
   if ((rs = ensure(&ctx->lbuf, &ctx->lbuf_cap, (size_t)n)) != RF_OK) return rs;
-  unsigned epoch;
+  const unsigned *epoch;
   if ((rs = adjoint_next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
   if (cudaMemsetAsync(ctl_words, 0, 6 * sizeof(unsigned), s) != cudaSuccess ||
       cudaMemsetAsync(&ctx->state->adj_sweeps, 0, sizeof(int), s) != cudaSuccess)

@@ -30,7 +30,7 @@ struct rf_ctx {
   size_t scratch_cap = 0;
   unsigned long long *adj_state = nullptr;  // adjoint (ordered): (epoch << 32 | lambda bits)
   size_t adj_state_cap = 0;
-  unsigned adj_epoch = 0;  // launch counter tagging adj_state words
+  unsigned adj_epoch = 0;  // host count of adjoint launches (the tag itself: DevState::adj_epoch)
   float4 *recbuf = nullptr;  // streamed sweep: node records, both orientations
   size_t recbuf_cap = 0;
   float *tvbuf = nullptr;  // total variation: per-block partial sums

@@ -213,6 +213,8 @@ struct DevState {
   unsigned max_res_bits;  // float bits of max |residual| (non-negative)
   unsigned rounds;        // rounds of the last tile-queue solve
   unsigned long long cell_updates;
+  unsigned adj_epoch;  // tag of the adjoint's per-node state words, bumped on the device per launch
+  unsigned pad;
 };
 
 __device__ __forceinline__ void set_error(DevState *st, int code) {

@@ -146,3 +146,38 @@ def test_tiles_timeout_returns_cleanly():
     assert ctx.stats()["status"] == 0
     g2, _ = api.rf_adjoint(src, T, rec, g, algo="ordered", ctx=ctx)
     assert torch.equal(g1.view(torch.int32), g2.view(torch.int32))
+
+
+@pytest.mark.parametrize("algo", ["tiles", "ordered"])
+def test_adjoint_graph_replay_with_new_inputs(algo):
+    """rf_adjoint captured in a CUDA graph: every replay tags its state words
+    anew (a device-side epoch), so a replay after dL/dT changed gives what a
+    direct call with the new dL/dT gives, bit for bit (a tag fixed at
+    capture would let the replay reuse the previous multipliers)."""
+    c = R.config2()
+    ctx = api.Context(0)
+    raw = to_dev(c["raw"], torch.float32)
+    src = to_dev(c["src"], torch.uint8)
+    proj, _ = api.rf_project(raw, c["eps"], c["delta"], ctx=ctx)
+    T, rec = api.rf_sweep_forward(proj, c["eps"], src, c["h"], ctx=ctx)
+    g = to_dev(c["g"], torch.float32)
+    ny, nx = T.shape
+    gproj = torch.empty((5, ny, nx), device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        api.rf_adjoint(src, T, rec, g, algo=algo, dLdproj5=gproj, ctx=ctx, stream=s)  # sizes the workspace
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            _, lam_g = api.rf_adjoint(src, T, rec, g, algo=algo, dLdproj5=gproj, ctx=ctx, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for k in range(3):
+        if k:
+            g.copy_(to_dev(R.sparse_loss_grad(ny, nx, 0.05, seed=100 + k), torch.float32))
+        want_g, want_l = api.rf_adjoint(src, T, rec, g, algo=algo, ctx=ctx)
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(gproj, want_g) and torch.equal(lam_g, want_l), k
+        assert ctx.stats()["status"] == 0

@@ -102,6 +102,20 @@ def test_batch_graph_replay_reproduces(variant):
     assert torch.equal(bs.T, T0)
     assert torch.equal(bs.graw, G0)
     assert int(bs.gstat[:, 0].abs().sum()) == 0
+    # new inputs between replays give what a run outside the graph gives
+    # (a replay that reused the previous replay's multipliers would not)
+    if bs.g is not None:
+        bs.g.mul_(-1.5)
+        graph, bs.graph = bs.graph, None
+        bs.run()
+        torch.cuda.synchronize()
+        want = bs.graw.clone()
+        bs.graph = graph
+        bs.graw.fill_(0.0)
+        bs.run()
+        torch.cuda.synchronize()
+        assert torch.equal(bs.graw, want)
+        assert not torch.equal(want, G0)
 
 
 @pytest.mark.parametrize("variant", ["tiles", "tiled1"])
