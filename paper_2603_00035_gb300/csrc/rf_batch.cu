@@ -447,8 +447,6 @@ rf_status batch_tiles(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids, int6
   if ((rs = cuda_status(cudaGetLastError())) != RF_OK) return rs;
   if (grid_status) batch_adj_status_kernel<<<blocks_for(n_grids, 256, 64), 256, 0, s>>>(grid_status, n_grids);
   if (!dLdT) return cuda_status(cudaGetLastError());
-  // the ordered gather: the tiled adjoint on packed grids of mixed sizes and
-  // many sources stalls on tiles waiting for tiles not yet taken
   return rf::adjoint_ordered(ctx, 0, 0, total_nodes, w.grids, n_grids, src, T, rec, dLdT, dLdproj5, nullptr, s);
 }
 
