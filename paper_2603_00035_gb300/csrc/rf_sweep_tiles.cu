@@ -61,7 +61,11 @@
 
 namespace rf {
 
-constexpr int kTileCta = 1024;     // threads per CTA (one or four tile groups)
+constexpr int kTileCta = 1024;     // threads per CTA with 32 x 32 tiles (one tile group)
+// threads per CTA with 16 x 16 tiles (four tile groups).  Fewer groups per
+// SM leave registers for each but fewer visits in flight: 2048^2 forward
+// 4.51 / 4.61 / 5.50 ms at 4 / 3 / 2 groups (window 2)
+constexpr int kTileCta16 = 1024;
 constexpr unsigned kInfBits = 0x7f800000u;
 constexpr int kSlots = 8;          // round slots (round mod 8)
 constexpr int kKeySlots = 4;       // queue-key slots (round mod 4)
@@ -93,12 +97,13 @@ struct TileGeom {
   static constexpr int TW = TS + 2;              // tile side with the halo ring
   static constexpr int HALO = 4 * TS + 4;        // halo ring nodes
   static constexpr int NODES = TS * TS;          // threads per group
-  static constexpr int GROUPS = kTileCta / NODES;
+  static constexpr int CTA = TS == 16 ? kTileCta16 : kTileCta;
+  static constexpr int GROUPS = CTA / NODES;
   static constexpr int TP = (TS == 32) ? 40 : 24;  // row pitch: rows 8 banks apart, so
                                                    // a warp's 4 x 8 patch hits 32 banks
   static constexpr int PCOLS = TS / 8;           // 8-column patches per row of patches
   static_assert(TS == 16 || TS == 32, "tile side");
-  static_assert(GROUPS * NODES == kTileCta, "groups fill the CTA");
+  static_assert(GROUPS * NODES == CTA, "groups fill the CTA");
 };
 
 // Shared memory of one tile group.
@@ -277,7 +282,7 @@ __device__ __forceinline__ void finish_end(const TileWork &w, int rg, unsigned o
 }
 
 template <int TS>
-__global__ void __launch_bounds__(kTileCta, 1) tile_solve_kernel(TileArgs a) {
+__global__ void __launch_bounds__(TileGeom<TS>::CTA, 1) tile_solve_kernel(TileArgs a) {
   using G = TileGeom<TS>;
   constexpr int NG = G::NODES;
   extern __shared__ float4 smem4[];
@@ -962,12 +967,13 @@ static rf_status launch_solve(TileArgs &a, int num_sms, cudaStream_t s) {
       cudaSuccess)
     return RF_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_solve_kernel<TS>, kTileCta, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_solve_kernel<TS>, TileGeom<TS>::CTA, smem) !=
+      cudaSuccess)
     return RF_ERR_CUDA;
   if (per_sm < 1) return RF_ERR_UNSUPPORTED;
   void *args[] = {&a};
   return cuda_status(cudaLaunchCooperativeKernel((const void *)tile_solve_kernel<TS>, dim3(per_sm * num_sms),
-                                                 dim3(kTileCta), args, smem, s));
+                                                 dim3(TileGeom<TS>::CTA), args, smem, s));
 }
 
 rf_status tiles_launch(const TileLaunch &L, const TileWork &w, const LaunchCtl &ctl, cudaStream_t s) {
