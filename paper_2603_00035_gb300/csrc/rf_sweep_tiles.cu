@@ -701,9 +701,8 @@ __global__ void tile_plan_single_kernel(TileWork w, int ny, int nx, float h, int
   g.tile_off = 0;
   g.h = h;
   g.inv_scale = 0.0f;
-  g.esum = 0.0f;
   g.has_src = 0;
-  g.pad = 0;
+  g.esum_fx = 0ull;
   w.grids[0] = g;
   w.ctrl[kCtrlNT] = (unsigned)(g.tny * g.tnx);
 }
@@ -765,9 +764,8 @@ __global__ void tile_plan_batch_kernel(TileWork w, const rf_batch_desc *descs, i
     t.tile_off = (int)off;
     t.h = any_bad ? 1.0f : d.h;
     t.inv_scale = 0.0f;
-    t.esum = 0.0f;
     t.has_src = 0;
-    t.pad = 0;
+    t.esum_fx = 0ull;
     w.grids[g] = t;
     off += (unsigned long long)t.tny * (unsigned long long)t.tnx;
   }
@@ -825,7 +823,9 @@ __global__ void tile_reset_kernel(TileArgs a) {
 // every tile (warm) or every tile that holds a source or one of its
 // neighbours (cold: a source never changes, so the tiles across a tile edge
 // next to it must see it in their halo on their own first visit).
-__global__ void tile_seed_kernel(TileArgs a) {
+constexpr int kSeedThreads = 256;
+
+__global__ void __launch_bounds__(kSeedThreads) tile_seed_kernel(TileArgs a) {
   const TileWork &w = a.w;
   const int NC = a.ntiles_cap;
   TGrid *gp = w.grids + blockIdx.y;
@@ -861,14 +861,31 @@ __global__ void tile_seed_kernel(TileArgs a) {
       w.list[(size_t)(1 % kSlots) * NC + t] = (1ull << 32) | (unsigned)t;
     }
   }
+  // the block's sum in a fixed order (warps, then the block's warps), then
+  // one integer atomic per block: the grid's sum, and the keys it scales,
+  // do not depend on the order in which blocks finish (a float atomic per
+  // warp also serialised 131 k atomics on one word at 2048^2)
+  __shared__ float wpart[kSeedThreads / 32];
+  __shared__ int wany[kSeedThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     part += __shfl_xor_sync(0xffffffffu, part, o);
     any_src |= __shfl_xor_sync(0xffffffffu, any_src, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&gp->esum, part);
-    if (any_src) atomicOr(&gp->has_src, 1);
+    wpart[threadIdx.x >> 5] = part;
+    wany[threadIdx.x >> 5] = any_src;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float bsum = 0.0f;
+    int bany = 0;
+    for (int k = 0; k < kSeedThreads / 32; ++k) {
+      bsum += wpart[k];
+      bany |= wany[k];
+    }
+    atomicAdd(&gp->esum_fx, (unsigned long long)((double)bsum * 4294967296.0 + 0.5));
+    if (bany) atomicOr(&gp->has_src, 1);
   }
 }
 
@@ -877,7 +894,8 @@ __global__ void tile_finish_seed_kernel(TileArgs a) {
   const TileWork &w = a.w;
   for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < a.n_grids; gi += gridDim.x * blockDim.x) {
     TGrid &g = w.grids[gi];
-    const float ebar = g.esum / (float)((long long)g.ny * g.nx);
+    const float esum = (float)((double)g.esum_fx * (1.0 / 4294967296.0));
+    const float ebar = esum / (float)((long long)g.ny * g.nx);
     g.inv_scale = (ebar > 0.0f && ebar < kInf) ? 1.0f / ((float)a.ts * ebar) : 1.0f;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1009,7 +1027,7 @@ rf_status tiles_launch(const TileLaunch &L, const TileWork &w, const LaunchCtl &
   const int reset_blocks = blocks_for((long long)L.ntiles_cap * (4 * ts + 4), 256, L.num_sms * 8);
   tile_reset_kernel<<<reset_blocks, 256, 0, s>>>(a);
   const int gx = std::max(1, std::min(blocks_for(per_grid, 256, L.num_sms * 8), 65535));
-  tile_seed_kernel<<<dim3(gx, L.n_grids), 256, 0, s>>>(a);
+  tile_seed_kernel<<<dim3(gx, L.n_grids), kSeedThreads, 0, s>>>(a);
   tile_finish_seed_kernel<<<blocks_for(L.n_grids, 256, 64), 256, 0, s>>>(a);
   const rf_status rs = ts == 32 ? launch_solve<32>(a, L.num_sms, s) : launch_solve<16>(a, L.num_sms, s);
   if (rs != RF_OK) return rs;

@@ -15,10 +15,11 @@ struct TGrid {
   int tile_off;        // first tile of the grid
   float h;             // spacing
   float inv_scale;     // 1 / (tile side x mean edge cost): keys in tile crossings
-  float esum;          // sum of the edge costs (seed)
   int has_src;         // the grid holds a source node
-  int pad;
+  unsigned long long esum_fx;  // sum of the edge costs (seed), fixed point (2^-32), order-independent
 };
+// (copied into each tile group's shared memory per visit: keep it 48 bytes)
+static_assert(sizeof(TGrid) == 48, "TGrid layout");
 
 // Per-solve workspace of the tile queue (one device allocation, carved).
 struct TileWork {
