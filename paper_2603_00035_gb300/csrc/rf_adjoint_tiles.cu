@@ -48,9 +48,14 @@ constexpr int kHalo = 4 * kTS + 4;         // halo nodes
 constexpr int kCompWarps = kNodes / 32;
 constexpr int kThreads = kNodes + 32;      // + the halo warp
 constexpr unsigned long long kTagMask = 0xffffffff00000000ull;
-constexpr unsigned kSpinFree = 1u << 30;  // polls of a stalled warp before it sleeps between polls
-constexpr unsigned kSleepNs = 200;
-constexpr int kCtasPerSm = 2;
+// A warp that has seen no progress for kSpinFree polls sleeps kSleepNs
+// between polls, leaving issue slots to the warps of other tiles that have
+// work; with that, three tiles per SM are in flight.  2048^2 workload:
+// 1.00 ms at two per SM without sleeping, 0.96 at three with 16 / 100 ns
+// (0.97 with 64 / 300, 1.04 with 16 / 200 at four).
+constexpr unsigned kSpinFree = 16;
+constexpr unsigned kSleepNs = 100;
+constexpr int kCtasPerSm = 3;
 
 struct TileAdjArgs {
   int ny, nx, tiles_x, n_tiles;
@@ -421,9 +426,9 @@ rf_status adjoint_tiles(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const f
     return RF_ERR_CUDA;
   // resident CTAs only (a cooperative launch checks it): a CTA that waits
   // for a tile held by a CTA that never started would only end by parking.
-  // Two per SM: the waiting warps of more tiles cost the working ones issue
-  // slots (2048^2 workload: 1.07 ms at two per SM, 1.70 at one, 2.53 at
-  // four)
+  // kCtasPerSm per SM: without sleeping stalled warps, more tiles in flight
+  // cost the working ones issue slots (1.07 ms at two per SM, 1.70 at one,
+  // 2.53 at four)
   const long long want = (n_tiles + 1) / 2;
   const int grid = (int)std::min<long long>((long long)std::min(per_sm, kCtasPerSm) * ctx->num_sms,
                                             std::max<long long>(want, 1));
