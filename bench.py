@@ -44,11 +44,12 @@ TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_
                    "paper_2603_00035_gb300/csrc/rf_sweep_common.cuh", "paper_2603_00035_gb300/csrc/rf_device.cuh"]
 # kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
 # source check, then tile queue: plan, reset, seed, finish-seed, solve, stats; streamed: node records +
-# sweep; tiled: sweep); the adjoint's (sweep: 1; ordered: keys, gather, unreached; tiles: tile keys,
-# tile gather -- CUB's sort kernels not counted)
+# sweep; tiled: sweep); the adjoint's (sweep: 1; ordered: epoch, keys, gather, unreached; levels: epoch,
+# keys, depth, starts, gather, unreached; tiles: epoch, tile keys, tile gather -- CUB's sort kernels not
+# counted)
 LAUNCHES_BASE = 3
 LAUNCHES_FORWARD = {8: 8, 2: 4, 1: 3, 4: 3}
-LAUNCHES_ADJOINT = {"sweep": 1, "ordered": 3, "levels": 5, "tiles": 2}
+LAUNCHES_ADJOINT = {"sweep": 1, "ordered": 4, "levels": 6, "tiles": 3}
 
 
 def parse():
