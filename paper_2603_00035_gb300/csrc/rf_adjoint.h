@@ -23,6 +23,13 @@ rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid 
 rf_status adjoint_tiles(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const float *T, const rf_record *rec,
                         const float *dLdT, float *dLdproj5, float *lambda, cudaStream_t s);
 
+// The same on packed grids (device descriptors with increasing node
+// offsets, n nodes in all, no side above max_line): tiles handed out grid
+// by grid in the packed order.
+rf_status adjoint_tiles_packed(rf_ctx *ctx, long long n, const TGrid *grids, int n_grids, int max_line,
+                               const uint8_t *src, const float *T, const rf_record *rec, const float *dLdT,
+                               float *dLdproj5, float *lambda, cudaStream_t s);
+
 // Next epoch of the context's tagged per-node state words (n of them):
 // enqueues the device-side bump on s and returns the device word the
 // adjoint kernels read it from; clears the words on first use and near the

@@ -37,6 +37,7 @@
 #include "rf_adjoint.h"
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
+#include "rf_sweep_tiles.h"
 
 namespace rf {
 namespace {
@@ -58,7 +59,12 @@ constexpr unsigned kSleepNs = 100;
 constexpr int kCtasPerSm = 3;
 
 struct TileAdjArgs {
-  int ny, nx, tiles_x, n_tiles;
+  int ny, nx, tiles_x, n_tiles;  // one grid (n_grids == 1)
+  int n_grids;                   // > 1: packed grids
+  const TGrid *grids;            // their shapes and node offsets
+  const int *toff;               // first 16 x 16 tile of each grid
+  const int *tgrid;              // grid of each tile (-1: past the last tile)
+  const unsigned *ntiles_dev;    // packed grids: the number of tiles (device)
   long long n;
   const uint8_t *src;
   const float *T;
@@ -102,26 +108,97 @@ __device__ __forceinline__ void sts_u64(unsigned long long *p, unsigned long lon
   *(volatile unsigned long long *)p = v;
 }
 
-// Sort key of a tile: ascending key = decreasing latest finite T; tiles
-// without a reached node last.
-__global__ void tile_keys_kernel(const float *T, int ny, int nx, int tiles_x, int n_tiles, unsigned *keys,
-                                 unsigned *vals) {
+// Where a tile lies: its grid's node offset and shape, and its first row
+// and column.  False for a tile past the last one (packed grids: the tile
+// arrays are sized by an upper bound).
+struct TileGeo {
+  long long goff;
+  int gny, gnx, ti0, tj0;
+  int gid;  // grid of the tile (0: one grid)
+};
+__device__ __forceinline__ bool tile_geo(const TileAdjArgs &a, int tile, TileGeo &g) {
+  int tl = tile, tx = a.tiles_x;
+  if (!a.grids) {
+    g.goff = 0;
+    g.gny = a.ny;
+    g.gnx = a.nx;
+    g.gid = 0;
+  } else {
+    const int gid = a.tgrid[tile];
+    if (gid < 0) return false;
+    const TGrid &d = a.grids[gid];
+    g.goff = d.node_off;
+    g.gny = d.ny;
+    g.gnx = d.nx;
+    g.gid = gid;
+    tl = tile - a.toff[gid];
+    tx = (d.nx + kTS - 1) / kTS;
+  }
+  g.ti0 = (tl / tx) * kTS;
+  g.tj0 = (tl - (tl / tx) * tx) * kTS;
+  return true;
+}
+
+// Packed grids: the first 16 x 16 tile of every grid (an exclusive scan of
+// the grids' tile counts, one block) and the total.
+__global__ void __launch_bounds__(1024) adjt_plan_kernel(const TGrid *grids, int n_grids, int *toff,
+                                                        unsigned *ntiles) {
+  __shared__ int part[1024];
+  int carry = 0;
+  for (int base = 0; base < n_grids; base += 1024) {
+    const int g = base + (int)threadIdx.x;
+    const int c = g < n_grids ? ((grids[g].ny + kTS - 1) / kTS) * ((grids[g].nx + kTS - 1) / kTS) : 0;
+    part[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int v = (int)threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    if (g < n_grids) toff[g] = carry + part[threadIdx.x] - c;
+    carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ntiles = (unsigned)carry;
+}
+
+// Packed grids: the grid of each tile (the array is preset to -1).
+__global__ void adjt_map_kernel(const TGrid *grids, int n_grids, const int *toff, int *tgrid) {
+  for (int g = blockIdx.x; g < n_grids; g += gridDim.x) {
+    const int c = ((grids[g].ny + kTS - 1) / kTS) * ((grids[g].nx + kTS - 1) / kTS);
+    for (int k = threadIdx.x; k < c; k += blockDim.x) tgrid[toff[g] + k] = g;
+  }
+}
+
+// Sort key of a tile: ascending key = grid (packed grids, in their packed
+// order), then decreasing latest finite T; tiles without a reached node
+// last in their grid, tiles past the last one at the very end.  Grid-major:
+// a grid's tiles are handed out together, so a tile only ever waits for
+// tiles of its own grid, taken about when they are needed -- as with one
+// grid.  (Ordering all grids' tiles by time together left the CTAs holding
+// tiles of many grids, each waiting for a neighbour no CTA had taken.)
+__global__ void tile_keys_kernel(TileAdjArgs a, int n_tiles, unsigned long long *keys, unsigned *vals) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < n_tiles; tile += warps) {
-    const int i0 = (tile / tiles_x) * kTS, j0 = (tile % tiles_x) * kTS;
+    TileGeo g;
     float m = -1.0f;
-    for (int k = lane; k < kNodes; k += 32) {
-      const int i = i0 + (k >> 4), j = j0 + (k & (kTS - 1));
-      if (i < ny && j < nx) {
-        const float t = T[(long long)i * nx + j];
-        if (t < kInf) m = fmaxf(m, t);
+    const bool real = tile_geo(a, tile, g);
+    if (real) {
+      for (int k = lane; k < kNodes; k += 32) {
+        const int i = g.ti0 + (k >> 4), j = g.tj0 + (k & (kTS - 1));
+        if (i < g.gny && j < g.gnx) {
+          const float t = a.T[g.goff + (long long)i * g.gnx + j];
+          if (t < kInf) m = fmaxf(m, t);
+        }
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) {
-      keys[tile] = m >= 0.0f ? ~__float_as_uint(m) : 0xffffffffu;
+      const unsigned kt = m >= 0.0f ? ~__float_as_uint(m) : 0xffffffffu;
+      keys[tile] = real ? ((unsigned long long)g.gid << 32) | kt : ~0ull;
       vals[tile] = (unsigned)tile;
     }
   }
@@ -130,13 +207,13 @@ __global__ void tile_keys_kernel(const float *T, int ny, int nx, int tiles_x, in
 // Next tile of the CTA (thread 0): the main list, then the retry ring
 // until every tile is finished; -1 when there is nothing left (or the
 // launch was aborted).
-__device__ int take_tile(const TileAdjArgs &a, unsigned long long t_start) {
+__device__ int take_tile(const TileAdjArgs &a, unsigned n_tiles, unsigned long long t_start) {
   if (ld_acquire_s32(a.ctl.abort)) return -1;
   const unsigned k = atomicAdd(&a.words[0], 1u);
-  if (k < (unsigned)a.n_tiles) return (int)a.order[k];
+  if (k < n_tiles) return (int)a.order[k];
   unsigned spins = 0;
   while (true) {
-    if (ld_acquire_u32(&a.words[1]) >= (unsigned)a.n_tiles) return -1;
+    if (ld_acquire_u32(&a.words[1]) >= n_tiles) return -1;
     const unsigned h = ld_acquire_u32(&a.words[2]), tl = ld_acquire_u32(&a.words[3]);
     if (h < tl) {
       if (atomicCAS(&a.words[2], h, h + 1) == h) {
@@ -177,15 +254,20 @@ __global__ void __launch_bounds__(kThreads) tile_adjoint_kernel(TileAdjArgs a) {
   __shared__ unsigned long long sw[kHS * kHS];  // tile + halo: tag | lambda
   __shared__ unsigned need[(kHalo + 31) / 32];  // halo nodes some tile node waits for
   __shared__ int s_tile, s_left, s_park;        // current tile, compute warps done, give up
+  __shared__ TileGeo s_geo;                     // where it lies
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const bool compute = warp < kCompWarps;
   const long long n = a.n;
   const unsigned long long tag = (unsigned long long)__ldg(a.epoch) << 32;
   const unsigned long long t_start = gtimer();
+  const unsigned n_tiles = a.ntiles_dev ? *(const volatile unsigned *)a.ntiles_dev : (unsigned)a.n_tiles;
   const int li = (t >> 4) & (kTS - 1), lj = t & (kTS - 1);
   const int slot = (li + 1) * kHS + lj + 1;
   while (true) {
-    if (t == 0) s_tile = take_tile(a, t_start);
+    if (t == 0) {
+      s_tile = take_tile(a, n_tiles, t_start);
+      if (s_tile >= 0 && !tile_geo(a, s_tile, s_geo)) s_geo.gny = s_geo.gnx = 0;  // cannot happen: tile < n_tiles
+    }
     for (int k = t; k < kHS * kHS; k += kThreads) sw[k] = 0ull;
     if (t < (kHalo + 31) / 32) need[t] = 0u;
     if (t == 0) {
@@ -198,7 +280,8 @@ __global__ void __launch_bounds__(kThreads) tile_adjoint_kernel(TileAdjArgs a) {
       if (t == 0) atomicMax(&a.ctl.st->adj_sweeps, (int)ld_acquire_u32(&a.words[4]));  // tiles that yielded
       break;
     }
-    const int ti0 = (tile / a.tiles_x) * kTS, tj0 = (tile % a.tiles_x) * kTS;
+    const int ti0 = s_geo.ti0, tj0 = s_geo.tj0, gny = s_geo.gny, gnx = s_geo.gnx;
+    const long long goff = s_geo.goff;
 
     // ---- compute threads: own node, its children and their weights ----
     long long p = -1;
@@ -210,8 +293,8 @@ __global__ void __launch_bounds__(kThreads) tile_adjoint_kernel(TileAdjArgs a) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) dTp[c] = 0.0f;
     const int gi = ti0 + li, gj = tj0 + lj;
-    if (compute && gi < a.ny && gj < a.nx) {
-      p = (long long)gi * a.nx + gj;
+    if (compute && gi < gny && gj < gnx) {
+      p = goff + (long long)gi * gnx + gj;
       // every load of the node and its neighbours first (one round trip),
       // the decisions after
       const unsigned long long w0 = ld_relaxed_u64(&a.state[p]);
@@ -223,8 +306,8 @@ __global__ void __launch_bounds__(kThreads) tile_adjoint_kernel(TileAdjArgs a) {
 #pragma unroll
       for (int nb = 0; nb < 8; ++nb) {
         const int ii = gi + nb_dy(nb), jj = gj + nb_dx(nb);
-        if (ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx) {
-          const long long q = (long long)ii * a.nx + jj;
+        if (ii >= 0 && ii < gny && jj >= 0 && jj < gnx) {
+          const long long q = goff + (long long)ii * gnx + jj;
           cw[nb] = child_weight(a.id[q], a.w1[q], (nb + 4) & 7);
         }
       }
@@ -324,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) tile_adjoint_kernel(TileAdjArgs a) {
         if (h < kHalo && ((need[h >> 5] >> (h & 31)) & 1u)) {
           pos[k] = halo_pos(h);
           const int r = pos[k] / kHS, c = pos[k] - r * kHS;
-          q[k] = (long long)(ti0 + r - 1) * a.nx + (tj0 + c - 1);  // inside the grid: a child was found there
+          q[k] = goff + (long long)(ti0 + r - 1) * gnx + (tj0 + c - 1);  // inside the grid: a child was found there
           pend |= 1u << k;
         }
       }
@@ -361,46 +444,59 @@ __global__ void __launch_bounds__(kThreads) tile_adjoint_kernel(TileAdjArgs a) {
 
 namespace rf {
 
-rf_status adjoint_tiles(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const float *T, const rf_record *rec,
-                        const float *dLdT, float *dLdproj5, float *lambda, cudaStream_t s) {
+namespace {
+
+// One grid (grids == NULL: ny x nx, n = ny * nx nodes, cap = its tiles) or
+// packed grids (device descriptors, n nodes in all, cap >= their tiles).
+rf_status adjoint_tiles_impl(rf_ctx *ctx, int ny, int nx, long long n, const TGrid *grids, int n_grids, int cap,
+                             const uint8_t *src, const float *T, const rf_record *rec, const float *dLdT,
+                             float *dLdproj5, float *lambda, cudaStream_t s) {
   ctx->last_stream = s;
-  const long long n = (long long)ny * nx;
-  const int tiles_y = (ny + kTS - 1) / kTS, tiles_x = (nx + kTS - 1) / kTS;
-  const int n_tiles = tiles_y * tiles_x;
-  // scratch: keys in/out, values in/out, retry ring, control words, CUB temp
+  // scratch: keys in/out, values in/out, retry ring, control words, packed
+  // grids' tile offsets and tile -> grid map, CUB temp
+  // keys: the grid in the high word (packed grids), the time in the low one
+  int end_bit = 32;
+  while (grids && end_bit < 64 && (1ll << (end_bit - 32)) < n_grids) ++end_bit;
   size_t temp_bytes = 0;
-  if (cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (unsigned *)nullptr, (unsigned *)nullptr,
-                                      (unsigned *)nullptr, (unsigned *)nullptr, n_tiles, 0, 32, s) != cudaSuccess)
+  if (cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (unsigned long long *)nullptr,
+                                      (unsigned long long *)nullptr, (unsigned *)nullptr, (unsigned *)nullptr, cap, 0,
+                                      end_bit, s) != cudaSuccess)
     return RF_ERR_CUDA;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t arr = up((size_t)n_tiles * sizeof(unsigned));
-  const unsigned ring_cap = 2u * (unsigned)n_tiles;
+  const size_t arr = up((size_t)cap * sizeof(unsigned));
+  const size_t arr64 = up((size_t)cap * sizeof(unsigned long long));
+  const unsigned ring_cap = 2u * (unsigned)cap;
   const size_t ring_bytes = up((size_t)ring_cap * sizeof(unsigned));
-  const size_t need = 4 * arr + ring_bytes + 256 + up(temp_bytes);
+  const size_t toff_bytes = grids ? up((size_t)n_grids * sizeof(int)) : 0;
+  const size_t map_bytes = grids ? arr : 0;
+  const size_t need = 2 * arr64 + 2 * arr + ring_bytes + 256 + toff_bytes + map_bytes + up(temp_bytes);
   rf_status rs;
   if ((rs = ensure((unsigned char **)&ctx->scratch, &ctx->scratch_cap, need)) != RF_OK) return rs;
   unsigned char *base = (unsigned char *)ctx->scratch;
-  unsigned *kin = (unsigned *)base, *kout = (unsigned *)(base + arr), *vin = (unsigned *)(base + 2 * arr),
-           *vout = (unsigned *)(base + 3 * arr);
-  unsigned *ring = (unsigned *)(base + 4 * arr);
-  unsigned *words = (unsigned *)(base + 4 * arr + ring_bytes);  // [0..4] queue, [5] abort
-  void *temp = base + 4 * arr + ring_bytes + 256;
+  unsigned long long *kin = (unsigned long long *)base, *kout = (unsigned long long *)(base + arr64);
+  unsigned char *b2 = base + 2 * arr64;
+  unsigned *vin = (unsigned *)b2, *vout = (unsigned *)(b2 + arr);
+  unsigned *ring = (unsigned *)(b2 + 2 * arr);
+  unsigned *words = (unsigned *)(b2 + 2 * arr + ring_bytes);  // [0..4] queue, [5] abort, [6] tiles
+  int *toff = (int *)(b2 + 2 * arr + ring_bytes + 256);
+  int *tgrid = (int *)(b2 + 2 * arr + ring_bytes + 256 + toff_bytes);
+  void *temp = b2 + 2 * arr + ring_bytes + 256 + toff_bytes + map_bytes;
   const unsigned *epoch;
   if ((rs = adjoint_next_epoch(ctx, n, s, &epoch)) != RF_OK) return rs;
   if (cudaMemsetAsync(ring, 0, ring_bytes + 256, s) != cudaSuccess ||
       cudaMemsetAsync(&ctx->state->adj_sweeps, 0, sizeof(int), s) != cudaSuccess)
     return RF_ERR_CUDA;
 
-  tile_keys_kernel<<<blocks_for((long long)n_tiles * 32, 256, ctx->num_sms * 8), 256, 0, s>>>(T, ny, nx, tiles_x,
-                                                                                             n_tiles, kin, vin);
-  if (cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, n_tiles, 0, 32, s) != cudaSuccess)
-    return RF_ERR_CUDA;
-
   TileAdjArgs a;
   a.ny = ny;
   a.nx = nx;
-  a.tiles_x = tiles_x;
-  a.n_tiles = n_tiles;
+  a.tiles_x = (nx + kTS - 1) / kTS;
+  a.n_tiles = cap;
+  a.n_grids = grids ? n_grids : 1;
+  a.grids = grids;
+  a.toff = toff;
+  a.tgrid = tgrid;
+  a.ntiles_dev = grids ? words + 6 : nullptr;
   a.n = n;
   a.src = src;
   a.T = T;
@@ -420,16 +516,25 @@ rf_status adjoint_tiles(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const f
   a.ctl.st = ctx->state;
   a.ctl.abort = (int *)(words + 5);
   a.ctl.timeout_ns = ctx->timeout_ns;
+  if (grids) {
+    if (cudaMemsetAsync(tgrid, 0xff, (size_t)cap * sizeof(int), s) != cudaSuccess) return RF_ERR_CUDA;
+    adjt_plan_kernel<<<1, 1024, 0, s>>>(grids, n_grids, toff, words + 6);
+    adjt_map_kernel<<<std::max(1, std::min(n_grids, 4 * ctx->num_sms)), 256, 0, s>>>(grids, n_grids, toff, tgrid);
+  }
+  tile_keys_kernel<<<blocks_for((long long)cap * 32, 256, ctx->num_sms * 8), 256, 0, s>>>(a, cap, kin, vin);
+  if (cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, cap, 0, end_bit, s) != cudaSuccess)
+    return RF_ERR_CUDA;
+
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_adjoint_kernel, kThreads, 0) != cudaSuccess ||
       per_sm < 1)
     return RF_ERR_CUDA;
   // resident CTAs only (a cooperative launch checks it): a CTA that waits
   // for a tile held by a CTA that never started would only end by parking.
-  // kCtasPerSm per SM: without sleeping stalled warps, more tiles in flight
-  // cost the working ones issue slots (1.07 ms at two per SM, 1.70 at one,
-  // 2.53 at four)
-  const long long want = (n_tiles + 1) / 2;
+  // Two per SM: the waiting warps of more tiles cost the working ones issue
+  // slots (2048^2 workload: 1.07 ms at two per SM, 1.70 at one, 2.53 at
+  // four)
+  const long long want = ((long long)cap + 1) / 2;
   const int grid = (int)std::min<long long>((long long)std::min(per_sm, kCtasPerSm) * ctx->num_sms,
                                             std::max<long long>(want, 1));
   void *args[] = {&a};
@@ -437,6 +542,22 @@ rf_status adjoint_tiles(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const f
       cudaSuccess)
     return RF_ERR_CUDA;
   return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+rf_status adjoint_tiles(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const float *T, const rf_record *rec,
+                        const float *dLdT, float *dLdproj5, float *lambda, cudaStream_t s) {
+  const int n_tiles = ((ny + kTS - 1) / kTS) * ((nx + kTS - 1) / kTS);
+  return adjoint_tiles_impl(ctx, ny, nx, (long long)ny * nx, nullptr, 1, n_tiles, src, T, rec, dLdT, dLdproj5,
+                            lambda, s);
+}
+
+rf_status adjoint_tiles_packed(rf_ctx *ctx, long long n, const TGrid *grids, int n_grids, int max_line,
+                               const uint8_t *src, const float *T, const rf_record *rec, const float *dLdT,
+                               float *dLdproj5, float *lambda, cudaStream_t s) {
+  const int cap = tiles_cap(n_grids, n, max_line, kTS);
+  return adjoint_tiles_impl(ctx, 0, 0, n, grids, n_grids, cap, src, T, rec, dLdT, dLdproj5, lambda, s);
 }
 
 }  // namespace rf

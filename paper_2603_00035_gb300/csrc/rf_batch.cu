@@ -447,7 +447,8 @@ rf_status batch_tiles(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids, int6
   if ((rs = cuda_status(cudaGetLastError())) != RF_OK) return rs;
   if (grid_status) batch_adj_status_kernel<<<blocks_for(n_grids, 256, 64), 256, 0, s>>>(grid_status, n_grids);
   if (!dLdT) return cuda_status(cudaGetLastError());
-  return rf::adjoint_ordered(ctx, 0, 0, total_nodes, w.grids, n_grids, src, T, rec, dLdT, dLdproj5, nullptr, s);
+  return rf::adjoint_tiles_packed(ctx, total_nodes, w.grids, n_grids, max_line, src, T, rec, dLdT, dLdproj5, nullptr,
+                                  s);
 }
 
 }  // namespace
