@@ -4,9 +4,10 @@
 // Two paths.  The default (variant AUTO or TILES) puts every grid's tiles in
 // one tile queue (rf_sweep_tiles.cu), so a large grid spreads over all SMs
 // while small ones finish in a few rounds, then records the stencils of all
-// grids in one pass and runs the ordered adjoint over the packed nodes (one
-// radix sort by decreasing T for all grids; a node's children are in its own
-// grid).  The line-sweep variants use the single persistent launch below.
+// grids in one pass and runs the tiled adjoint over the packed grids
+// (rf_adjoint_tiles.cu: 16 x 16 tiles handed out a few grids at a time; a
+// node's children are in its own grid).  The line-sweep variants use the
+// single persistent launch below.
 //
 // Paper: the batched solves of Sec. 3.4 ("batched approach proves
 // essential"), with the same discrete system as rf_sweep_forward / rf_adjoint
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(256) batch_record_kernel(const TGrid *grids, l
   if ((threadIdx.x & 31) == 0) atomicMax(&st->max_res_bits, __float_as_uint(local_max));
 }
 
-// Adjoint column of the per-grid status (the ordered adjoint has no sweeps).
+// Adjoint column of the per-grid status (the tiled adjoint has no sweeps).
 __global__ void batch_adj_status_kernel(int *gstat, int n_grids) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_grids; g += gridDim.x * blockDim.x)
     gstat[3 * g + 2] = 0;
