@@ -20,7 +20,6 @@
 #include "rf_adjoint.h"
 #include "rf_ctx.h"
 #include "rf_sweep_common.cuh"
-#include "rf_sweep_tiles.h"
 
 namespace rf {
 
@@ -262,10 +261,8 @@ __global__ void ordered_keys_kernel(const float *T, unsigned *keys, unsigned *va
 }
 
 struct OrderedArgs {
-  int ny, nx;             // one grid (n_grids == 1)
-  long long n;            // nodes of all grids (plane stride of dT and grad)
-  int n_grids;            // > 1: packed grids, geometry in grids[] (node offsets increasing)
-  const TGrid *grids;
+  int ny, nx;
+  long long n;            // ny * nx (plane stride of dT and grad)
   const uint8_t *src;
   const float *T;
   const uint8_t *id;
@@ -280,17 +277,6 @@ struct OrderedArgs {
   float *lam_out;
   LaunchCtl ctl;
 };
-
-// Grid of packed node p: the last grid whose first node is <= p.
-__device__ __forceinline__ int grid_of(const TGrid *grids, int n_grids, long long p) {
-  int lo = 0, hi = n_grids - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&grids[mid].node_off) <= p) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
 __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
   const int lane = threadIdx.x & 31;
@@ -309,19 +295,12 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
     float gsum = 0.0f;
     float dTp[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // partials, loaded before the wait
     bool act = false;
-    int pi = 0, pj = 0, gny = a.ny, gnx = a.nx;
-    long long goff = 0;
+    int pi = 0, pj = 0;
+    const int gny = a.ny, gnx = a.nx;
     if (!done) {
       p = a.order[pos];
-      if (a.n_grids > 1) {
-        const int g = grid_of(a.grids, a.n_grids, p);
-        goff = __ldg(&a.grids[g].node_off);
-        gny = __ldg(&a.grids[g].ny);
-        gnx = __ldg(&a.grids[g].nx);
-      }
-      const long long lp = p - goff;
-      pi = gnx > 0 ? (int)(lp / gnx) : 0;  // gnx = 0: the grids of an invalid batch were emptied
-      pj = (int)(lp - (long long)pi * gnx);
+      pi = (int)(p / gnx);
+      pj = (int)(p - (long long)pi * gnx);
       const float tp = a.T[p];
       if (!(tp < kInf)) {
         // unreached: no residual, no children
@@ -339,7 +318,7 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
       cw[nb] = 0.0f;
       const int ii = pi + nb_dy(nb), jj = pj + nb_dx(nb);
       if (!done && ii >= 0 && ii < gny && jj >= 0 && jj < gnx) {
-        const long long qn = goff + (long long)ii * gnx + jj;
+        const long long qn = (long long)ii * gnx + jj;
         cw[nb] = child_weight(a.id[qn], a.w1[qn], (nb + 4) & 7);
         if (cw[nb] != 0.0f) cmask |= 1u << nb;
       }
@@ -353,7 +332,7 @@ __global__ void __launch_bounds__(256) ordered_gather_kernel(OrderedArgs a) {
 #pragma unroll
         for (int nb = 0; nb < 8; ++nb) {
           if (cmask & (1u << nb)) {
-            const long long qn = goff + (long long)(pi + nb_dy(nb)) * gnx + (pj + nb_dx(nb));
+            const long long qn = (long long)(pi + nb_dy(nb)) * gnx + (pj + nb_dx(nb));
             const unsigned long long v = ld_relaxed_u64(&a.state[qn]);
             ready = ready && ((v & 0xffffffff00000000ull) == tag);
             acc = fmaf(cw[nb], __uint_as_float((unsigned)v), acc);
@@ -662,13 +641,11 @@ rf_status adjoint_next_epoch(rf_ctx *ctx, long long n, cudaStream_t s, const uns
   return cuda_status(cudaGetLastError());
 }
 
-// The ordered adjoint of one grid (grids == NULL: shape ny x nx) or of
-// packed grids (grids: device descriptors with increasing node offsets, n
-// nodes in all).
-rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid *grids, int n_grids,
-                          const uint8_t *src, const float *T, const rf_record *rec, const float *dLdT,
-                          float *dLdproj5, float *lambda, cudaStream_t s) {
+// The ordered adjoint of one ny x nx grid.
+rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const float *T, const rf_record *rec,
+                          const float *dLdT, float *dLdproj5, float *lambda, cudaStream_t s) {
   ctx->last_stream = s;
+  const long long n = (long long)ny * nx;
   // scratch: keys in/out, values in/out, ticket, abort flag, CUB temp
   size_t temp_bytes = 0;
   if (cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (unsigned *)nullptr, (unsigned *)nullptr,
@@ -695,8 +672,6 @@ rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid 
   a.ny = ny;
   a.nx = nx;
   a.n = n;
-  a.n_grids = grids ? n_grids : 1;
-  a.grids = grids;
   a.src = src;
   a.T = T;
   a.id = rec->id;
@@ -833,8 +808,7 @@ extern "C" rf_status rf_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t 
   if (algo == RF_ADJ_LEVELS)
     return rf::adjoint_levels(ctx, grid->ny, grid->nx, src, T, rec, dLdT, dLdproj5, lambda, (cudaStream_t)stream);
   if (algo == RF_ADJ_ORDERED)
-    return rf::adjoint_ordered(ctx, grid->ny, grid->nx, (long long)grid->ny * grid->nx, nullptr, 1, src, T, rec,
-                               dLdT, dLdproj5, lambda, (cudaStream_t)stream);
+    return rf::adjoint_ordered(ctx, grid->ny, grid->nx, src, T, rec, dLdT, dLdproj5, lambda, (cudaStream_t)stream);
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
   const int ny = grid->ny, nx = grid->nx;

@@ -1,6 +1,6 @@
-// rf_adjoint.h -- internal interface of the ordered adjoint (rf_adjoint.cu),
-// used by rf_adjoint and by the tile-queue path of rf_batch_solve, and of
-// the tiled adjoint (rf_adjoint_tiles.cu).
+// rf_adjoint.h -- internal interface of the ordered adjoint (rf_adjoint.cu)
+// and of the tiled adjoint (rf_adjoint_tiles.cu), used by rf_adjoint,
+// rf_step_host and the tile-queue path of rf_batch_solve.
 #pragma once
 
 #include "rf_ctx.h"
@@ -9,13 +9,11 @@ namespace rf {
 
 struct TGrid;
 
-// Alg. 2 on one grid (grids == NULL: shape ny x nx, n = ny * nx) or on
-// packed grids (grids: device descriptors with increasing node offsets, n
-// nodes in all): radix sort by decreasing T, then the dependency-ordered
-// gather; writes dLdproj5 (5 planes of stride n) and lambda (nullable).
-rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, long long n, const TGrid *grids, int n_grids,
-                          const uint8_t *src, const float *T, const rf_record *rec, const float *dLdT,
-                          float *dLdproj5, float *lambda, cudaStream_t s);
+// Alg. 2 on one ny x nx grid: radix sort by decreasing T, then the
+// dependency-ordered gather; writes dLdproj5 (5 planes of stride ny * nx)
+// and lambda (nullable).
+rf_status adjoint_ordered(rf_ctx *ctx, int ny, int nx, const uint8_t *src, const float *T, const rf_record *rec,
+                          const float *dLdT, float *dLdproj5, float *lambda, cudaStream_t s);
 
 // Alg. 2 on one grid with the dependency chain followed inside 16 x 16
 // tiles in shared memory (RF_ADJ_TILES); same outputs as adjoint_ordered,
