@@ -437,13 +437,14 @@ rf_status rf_softmin_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *sr
  * word).  descs: DEVICE array of n_grids descriptors; put the largest grid
  * first.  max_line >= every grid's max(ny, nx).  T, rec: outputs (rec
  * required; the adjoint reads it).  dLdT (nullable) and dLdproj5: packed
- * like T and proj5.  grid_status (DEVICE, nullable): 3 int32 per grid =
- * status, forward sweeps (TILES: node updates / nodes, rounded up), adjoint
- * sweeps (0 for the tiled adjoint).
+ * like T and proj5; rec and dLdproj5 are not written between grids.
+ * grid_status (DEVICE, nullable): 3 int32 per grid = status, forward sweeps
+ * (TILES: node updates / nodes, rounded up), adjoint sweeps (0 for the
+ * tiled adjoint).
  * opts->variant AUTO or TILES: every grid's tiles share one tile queue (see
  * RF_SWEEP_TILES; band = tile side), then one record pass and the tiled
- * adjoint over the packed grids (RF_ADJ_TILES, tiles handed out eight grids
- * at a time) -- a few launches on `stream`.  Line-sweep
+ * adjoint over the packed grids (RF_ADJ_TILES, tiles handed out eight
+ * grids at a time) -- a few launches on `stream`.  Line-sweep
  * variants: one persistent launch, CTAs taking whole grids in array order,
  * the transposed-sweep adjoint; max_line <= 1024 (shared-memory lines).
  * Both allocate only on first use (workspace grown to the call's size);
