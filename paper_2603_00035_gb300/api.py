@@ -266,7 +266,7 @@ def rf_residual(proj5, eps, src, h, T, per_node=False, ctx=None, stream=None):
     return (mx, res) if per_node else mx
 
 
-def rf_adjoint(src, T, rec, dLdT, algo="sweep", lam=True, dLdproj5=None, ctx=None, stream=None):
+def rf_adjoint(src, T, rec, dLdT, algo="tiles", lam=True, dLdproj5=None, ctx=None, stream=None):
     """a6-a8: solve J^T lambda = g on the recorded stencils and contract with
     the partials.  algo: a name of ADJ_ALGOS.  Returns (dL/d(L11,
     L21, L22, wx, wy) of the projected fields, lambda or None)."""

@@ -49,7 +49,7 @@ def to_dev(a, dtype=None):
     return t.cuda()
 
 
-def gpu_path(raw, src, h, eps, delta, g, opts=None, algo="sweep"):
+def gpu_path(raw, src, h, eps, delta, g, opts=None, algo="tiles"):
     """project -> forward (+record) -> adjoint -> project backward on the GPU."""
     raw_t = to_dev(raw, torch.float32)
     src_t = to_dev(src, torch.uint8)

@@ -44,7 +44,7 @@ def target_times(raw_shape, src, h, eps, delta, seed):
 
 
 @pytest.mark.parametrize("which", ["config1", "crop256"])
-@pytest.mark.parametrize("algo", ["ordered", "sweep"])
+@pytest.mark.parametrize("algo", ["tiles", "ordered", "sweep"])
 def test_rfsolve_gradients_match_oracle(which, algo):
     if which == "config1":
         c = R.config1()

@@ -116,7 +116,7 @@ def test_ordered_adjoint_matches_sweep_and_oracle(case):
     assert rel_l2(gproj, orc["gproj"], ~flips) < GRAD_TOL
 
 
-@pytest.mark.parametrize("algo", ["sweep", "ordered"])
+@pytest.mark.parametrize("algo", ["sweep", "ordered", "tiles"])
 def test_adjoint_kernel_on_oracle_record(algo):
     """The adjoint kernel alone, fed the oracle's record (cast to float32):
     lambda and the contracted gradients must match the FP64 back-substitution
@@ -205,7 +205,7 @@ def test_timeout_path_returns_cleanly():
     st = ctx.stats()
     assert st["status"] == 0 and st["converged"]
     g = to_dev(c["g"], torch.float32)
-    for algo in ("sweep", "ordered"):
+    for algo in ("sweep", "ordered", "tiles"):
         ctx.set_timeout(0)
         api.rf_adjoint(src, T, rec, g, algo=algo, ctx=ctx)
         assert ctx.stats()["status"] == 4, algo  # RF_ERR_TIMEOUT
