@@ -704,11 +704,15 @@ def run_softmin(args):
     proj, _ = api.rf_project(raw, c["eps"], c["delta"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    # forward: the tile queue with the soft-min update (variant 0 / 8), or a
+    # line-sweep variant's number for Jacobi iterations over the whole grid
+    sopts = api.make_opts(variant=args.variant)
+    tile_fwd = args.variant in (0, 8)
 
     def step(timed):
         if timed:
             ev[0].record()
-        T = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau)
+        T = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau, opts=sopts)
         if timed:
             ev[1].record()
         wnb, dT = api.rf_softmin_record(proj, c["eps"], src, c["h"], T, tau)
@@ -739,7 +743,9 @@ def run_softmin(args):
             "config": {"workload": f"soft-min relaxation, {n}x{n} inverse-problem fields, tau = {args.tau_rel} h",
                        "l2": "flushed between timed steps (256 MB write)"},
             "phase_ms": {"forward": ph[0], "record": ph[1], "adjoint": ph[2]},
-            "jacobi_iterations": iters, "adjoint_iterations": adj, "gpu_launches": 6 * args.steps}
+            "forward": "tile queue" if tile_fwd else "Jacobi over the grid",
+            "forward_sweeps": iters, "adjoint_iterations": adj,
+            "gpu_launches": (10 if tile_fwd else 5) * args.steps}
     print(json.dumps(line), flush=True)
 
 

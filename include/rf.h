@@ -401,12 +401,14 @@ rf_status rf_step_host(rf_ctx *ctx, const rf_grid *grid, int n_steps,
  * values run to -inf -- reported as RF_ERR_NOT_CONVERGED as soon as a
  * non-source node goes negative.
  *
- * rf_softmin_forward: Jacobi iterations of the relaxed system (all nodes,
- * one persistent launch) from T = 0 on sources, +inf elsewhere (warm mode:
- * the caller's T), until an iteration changes no node by more than tol +
- * rtol |T| (opts as rf_sweep_forward; at most max_sweeps x max(ny, nx)
- * iterations; the iteration count is reported as the sweeps statistic).
- * Arguments as rf_sweep_forward without the record. */
+ * rf_softmin_forward: the relaxed system solved from T = 0 on sources,
+ * +inf elsewhere (warm mode: the caller's T) until no node would change by
+ * more than tol + rtol |T| (opts as rf_sweep_forward).  opts->variant AUTO
+ * or TILES: the tile queue of RF_SWEEP_TILES with the soft-min update (the
+ * sweeps statistic is node updates / nodes); a line-sweep variant: Jacobi
+ * iterations over all nodes in one persistent launch (at most max_sweeps x
+ * max(ny, nx) iterations, reported as the sweeps statistic).  Arguments as
+ * rf_sweep_forward without the record. */
 rf_status rf_softmin_forward(rf_ctx *ctx, const rf_grid *grid, const float *proj5, float eps,
                              const uint8_t *src, float tau, const rf_opts *opts, float *T, void *stream);
 /* Record of the relaxed system at T: wnb (8 planes, [8][ny*nx]) =

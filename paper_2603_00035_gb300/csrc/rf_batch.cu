@@ -438,6 +438,7 @@ rf_status batch_tiles(rf_ctx *ctx, const rf_batch_desc *descs, int n_grids, int6
   L.tol = o.tol;
   L.rtol = o.rtol;
   L.window = o.window;
+  L.tau = 0.0f;
   L.grid_status = grid_status;
   if ((rs = rf::tiles_launch(L, w, ctl, s)) != RF_OK) return rs;
   cudaMemsetAsync(&ctx->state->max_res_bits, 0, sizeof(unsigned), s);

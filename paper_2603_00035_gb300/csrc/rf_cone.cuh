@@ -110,6 +110,45 @@ __device__ __forceinline__ float cone_min(const float4 &q0, const float4 &q1, co
   return cand;
 }
 
+// Soft-min relaxation (Sec. 3.3; the reading of rf_softmin.cu) in the cone
+// form: every stencil k has the value of its segment minimum -- the valid
+// two-point candidate, else the smaller one-point candidate of its
+// endpoints -- and the node takes -tau log sum_k exp(-v_k / tau) (the hard
+// minimum when tau = 0; +inf when no stencil has a finite value).
+__device__ __forceinline__ float cone_softmin(const float4 &q0, const float4 &q1, const float4 &q2,
+                                              const float4 &q3, const float4 &q4, const float4 &q5,
+                                              const float Tn[8], float tau) {
+  const float len[4] = {fabsf(q0.x), q0.y, q0.z, q0.w};
+  const float wm[4] = {q1.x, q1.y, q1.z, q1.w};
+  const float C[4] = {q3.x, q3.y, q3.z, q3.w};
+  const float mid[4] = {q4.x, q4.y, q4.z, q4.w};
+  const float hw[4] = {q5.x, q5.y, q5.z, q5.w};
+  float S[8], one[8], v[8];
+#pragma unroll
+  for (int nb = 0; nb < 8; ++nb) {
+    S[nb] = (nb < 4) ? Tn[nb] - wm[nb] : Tn[nb] + wm[nb - 4];
+    one[nb] = S[nb] + len[len_class(nb)];
+  }
+  float vmin = kInf;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int a = k, b = (k + 1) & 7, p = k & 3;
+    const bool xs = (k & 2) != 0;
+    const float Pk = xs ? q2.x : q2.z, Qk = xs ? q2.y : q2.w;
+    const float d = S[b] - S[a];
+    const float q = fmaf(-Qk, d * d, Pk);
+    const float T0 = fmaf(C[p], d, S[a]) + q * rsqrt_ftz(q);
+    const bool ok = (fabsf(d - mid[p]) < hw[p]) && (fmaxf(Tn[a], Tn[b]) < T0);
+    v[k] = ok ? T0 : fminf(one[a], one[b]);
+    vmin = fminf(vmin, v[k]);
+  }
+  if (!(vmin < kInf) || !(tau > 0.0f)) return vmin;
+  float sum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += (v[k] < kInf) ? expf((vmin - v[k]) / tau) : 0.0f;
+  return vmin - tau * logf(sum);
+}
+
 // Stencil record of node (i, j) at the converged T in the cone form (Alg. 2
 // first loop; App. A closed-form partials): one pass over the 16 candidates
 // gives both the plain minimum (for the residual r = T - min valid

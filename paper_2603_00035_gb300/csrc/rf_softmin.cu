@@ -332,6 +332,52 @@ extern "C" rf_status rf_softmin_forward(rf_ctx *ctx, const rf_grid *grid, const 
   const int ny = grid->ny, nx = grid->nx;
   const long long n = (long long)ny * nx;
   rf_status rs;
+  if (o.variant == RF_SWEEP_AUTO || o.variant == RF_SWEEP_TILES) {
+    // the tile queue (rf_sweep_tiles.cu) with the soft-min update: Jacobi
+    // inside 16 x 16 tiles, rounds over the tiles the front reaches
+    const int ts = tile_side(o.variant == RF_SWEEP_TILES ? o.band : 0);
+    const int ncap = tiles_cap(1, n, std::max(ny, nx), ts);
+    if ((rs = ensure(&ctx->tilebuf, &ctx->tilebuf_cap, tile_work_bytes(1, ncap, ts))) != RF_OK) return rs;
+    if ((rs = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)n)) != RF_OK) return rs;
+    if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)o.max_sweeps + 2)) != RF_OK) return rs;
+    cudaMemsetAsync(ctx->changed, 0, sizeof(int) * (o.max_sweeps + 2), s);
+    cudaMemsetAsync(&ctx->state->sweeps, 0, sizeof(int) * 2, s);
+    cudaMemsetAsync(&ctx->state->bar, 0, sizeof(unsigned long long) + 2 * sizeof(unsigned), s);
+    cudaMemsetAsync(&ctx->state->cell_updates, 0, sizeof(unsigned long long), s);
+    int *has_src = ctx->changed + o.max_sweeps;
+    init_state(T, src, n, o.mode == RF_MODE_WARM, ctx->state, has_src, ctx->num_sms, s);
+    check_source_flag(has_src, ctx->state, s);
+    LaunchCtl ctl;
+    ctl.st = ctx->state;
+    ctl.abort = ctx->changed + o.max_sweeps + 1;
+    ctl.timeout_ns = ctx->timeout_ns;
+    const TileWork w = tile_work_carve(ctx->tilebuf, 1, ncap, ts);
+    TileLaunch L;
+    L.num_sms = ctx->num_sms;
+    L.ts = ts;
+    L.n_grids = 1;
+    L.descs = nullptr;
+    L.ny = ny;
+    L.nx = nx;
+    L.h = grid->h;
+    L.max_line = std::max(ny, nx);
+    L.total_nodes = n;
+    L.ntiles_cap = ncap;
+    L.eps = eps;
+    L.proj5 = proj5;
+    L.src = src;
+    L.T = T;
+    L.Tb = ctx->tbuf;
+    L.warm = o.mode == RF_MODE_WARM;
+    L.max_sweeps = o.max_sweeps;
+    L.tol = o.tol;
+    L.rtol = o.rtol;
+    L.window = o.window;
+    L.tau = tau;
+    L.grid_status = nullptr;
+    return tiles_launch(L, w, ctl, s);
+  }
+  // the line-sweep variants select Jacobi iterations over the whole grid
   if ((rs = ensure(&ctx->tbuf, &ctx->tbuf_cap, (size_t)n)) != RF_OK) return rs;
   if ((rs = ensure(&ctx->changed, &ctx->changed_cap, (size_t)8)) != RF_OK) return rs;
   cudaMemsetAsync(ctx->changed, 0, sizeof(int) * 8, s);

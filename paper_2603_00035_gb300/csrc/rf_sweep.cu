@@ -591,6 +591,7 @@ extern "C" rf_status rf_sweep_forward(rf_ctx *ctx, const rf_grid *grid, const fl
       L.tol = o.tol;
       L.rtol = o.rtol;
       L.window = o.window;
+      L.tau = 0.0f;
       L.grid_status = nullptr;
       rt = rf::tiles_launch(L, w, ctl, s);
       if (rt != RF_OK) return rt;

@@ -132,6 +132,7 @@ struct TileArgs {
   float *T[2];  // buffer 0 = the caller's T, buffer 1 = workspace
   float tol, rtol;
   float window;  // delta-stepping window in tile crossings
+  float tau;     // soft-min temperature (the SOFT kernels only)
   int warm;
   int max_rounds, max_local;
   TileWork w;
@@ -281,7 +282,10 @@ __device__ __forceinline__ void finish_end(const TileWork &w, int rg, unsigned o
   if (old + 1u == kPrevDone) complete_round(w, rg, ntiles_all, max_rounds);
 }
 
-template <int TS>
+// SOFT: the node update is the soft-min relaxation (cone_softmin; a value
+// below zero means no finite fixed point: RF_ERR_NOT_CONVERGED, the launch
+// stops) instead of the minimum.
+template <int TS, bool SOFT>
 __global__ void __launch_bounds__(TileGeom<TS>::CTA, 1) tile_solve_kernel(TileArgs a) {
   using G = TileGeom<TS>;
   constexpr int NG = G::NODES;
@@ -572,7 +576,16 @@ __global__ void __launch_bounds__(TileGeom<TS>::CTA, 1) tile_solve_kernel(TileAr
             float Tn[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) Tn[k] = S.Ts[cb][sr + nb_dy(k)][sc + nb_dx(k)];
-            tnew = cone_min(S.q[0][gt], S.q[1][gt], S.q[2][gt], S.q[3][gt], S.q[4][gt], S.q[5][gt], Tn);
+            if constexpr (SOFT) {
+              tnew = cone_softmin(S.q[0][gt], S.q[1][gt], S.q[2][gt], S.q[3][gt], S.q[4][gt], S.q[5][gt], Tn,
+                                  a.tau);
+              if (tnew < 0.0f) {
+                set_error(a.ctl.st, RF_ERR_NOT_CONVERGED);
+                atomicExch(a.ctl.abort, 1);
+              }
+            } else {
+              tnew = cone_min(S.q[0][gt], S.q[1][gt], S.q[2][gt], S.q[3][gt], S.q[4][gt], S.q[5][gt], Tn);
+            }
           }
           if (lane == 0) {
             atomicAdd(&S.upd, (unsigned)__popc(dball));
@@ -978,19 +991,19 @@ TileWork tile_work_carve(void *base, int n_grids, int ntiles_cap, int ts) {
   return w;
 }
 
-template <int TS>
+template <int TS, bool SOFT>
 static rf_status launch_solve(TileArgs &a, int num_sms, cudaStream_t s) {
   const size_t smem = sizeof(GroupSmem<TS>) * TileGeom<TS>::GROUPS;
-  if (cudaFuncSetAttribute(tile_solve_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(tile_solve_kernel<TS, SOFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return RF_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_solve_kernel<TS>, TileGeom<TS>::CTA, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_solve_kernel<TS, SOFT>, TileGeom<TS>::CTA, smem) !=
       cudaSuccess)
     return RF_ERR_CUDA;
   if (per_sm < 1) return RF_ERR_UNSUPPORTED;
   void *args[] = {&a};
-  return cuda_status(cudaLaunchCooperativeKernel((const void *)tile_solve_kernel<TS>, dim3(per_sm * num_sms),
+  return cuda_status(cudaLaunchCooperativeKernel((const void *)tile_solve_kernel<TS, SOFT>, dim3(per_sm * num_sms),
                                                  dim3(TileGeom<TS>::CTA), args, smem, s));
 }
 
@@ -1010,6 +1023,7 @@ rf_status tiles_launch(const TileLaunch &L, const TileWork &w, const LaunchCtl &
   a.rtol = L.rtol;
   a.window = L.window > 0.0f ? L.window : (ts == 32 ? 2.0f : 4.0f);
   a.warm = L.warm;
+  a.tau = L.tau;
   // a sweep moves information across the grid, a round across one tile
   a.max_rounds = L.max_sweeps * std::max(1, (L.max_line + ts - 1) / ts);
   a.max_local = 16 * ts;
@@ -1029,7 +1043,9 @@ rf_status tiles_launch(const TileLaunch &L, const TileWork &w, const LaunchCtl &
   const int gx = std::max(1, std::min(blocks_for(per_grid, 256, L.num_sms * 8), 65535));
   tile_seed_kernel<<<dim3(gx, L.n_grids), kSeedThreads, 0, s>>>(a);
   tile_finish_seed_kernel<<<blocks_for(L.n_grids, 256, 64), 256, 0, s>>>(a);
-  const rf_status rs = ts == 32 ? launch_solve<32>(a, L.num_sms, s) : launch_solve<16>(a, L.num_sms, s);
+  const bool soft = L.tau > 0.0f;
+  const rf_status rs = ts == 32 ? (soft ? launch_solve<32, true>(a, L.num_sms, s) : launch_solve<32, false>(a, L.num_sms, s))
+                                : (soft ? launch_solve<16, true>(a, L.num_sms, s) : launch_solve<16, false>(a, L.num_sms, s));
   if (rs != RF_OK) return rs;
   tile_stats_kernel<<<blocks_for(L.n_grids, 256, 64), 256, 0, s>>>(a, ctl.st, L.grid_status, 0);
   return cuda_status(cudaGetLastError());

@@ -54,6 +54,7 @@ struct TileLaunch {
   float *T, *Tb;
   int warm, max_sweeps;
   float tol, rtol, window;
+  float tau;                     // > 0: the soft-min relaxation instead of the minimum
   int *grid_status;              // batch: [3 * grids] status, forward sweep equivalent (adjoint left alone)
 };
 

@@ -31,9 +31,10 @@ def ragged():
 CASES = {"config1": R.config1, "ragged": ragged}
 
 
+@pytest.mark.parametrize("variant", ["tiles", "tiled1"])  # tile queue; Jacobi over the grid
 @pytest.mark.parametrize("which", list(CASES))
 @pytest.mark.parametrize("rel_tau", [0.002, 0.05])
-def test_softmin_solve_record_and_gradient_match_oracle(which, rel_tau):
+def test_softmin_solve_record_and_gradient_match_oracle(which, rel_tau, variant):
     c = CASES[which]()
     tau = rel_tau * c["h"]
     orc = O.softmin_solve_and_grad(c["raw"].astype(np.float64), c["src"], c["h"], c["eps"], c["delta"],
@@ -42,7 +43,7 @@ def test_softmin_solve_record_and_gradient_match_oracle(which, rel_tau):
     raw = to_dev(c["raw"], torch.float32)
     src = to_dev(c["src"], torch.uint8)
     proj, clip = api.rf_project(raw, c["eps"], c["delta"])
-    T = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau)
+    T = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau, opts=api.make_opts(variant=variant))
     st = api.Context.get(0).stats()
     assert st["status"] == 0 and st["converged"], st
     Tg, To = T.cpu().numpy(), orc["T"]
@@ -107,7 +108,26 @@ def test_too_large_tau_is_reported_not_run_forever():
     raw = to_dev(c["raw"], torch.float32)
     src = to_dev(c["src"], torch.uint8)
     proj, _ = api.rf_project(raw, c["eps"], c["delta"])
-    api.rf_softmin_forward(proj, c["eps"], src, c["h"], 2.0 * c["h"])
+    for variant in ("tiles", "tiled1"):
+        api.rf_softmin_forward(proj, c["eps"], src, c["h"], 2.0 * c["h"], opts=api.make_opts(variant=variant))
+        st = api.Context.get(0).stats()
+        assert st["status"] == L.RF_ERR_NOT_CONVERGED, variant
+        assert st["sweeps"] < 64 * 64, variant  # stopped early, not at the iteration cap
+
+
+def test_softmin_tile_queue_equals_jacobi_at_512():
+    """The 512^2 workload: the tile queue and the Jacobi iterations solve the
+    same relaxed system (within the stopping tolerance), deterministically."""
+    c = R.config2()
+    tau = 0.05 * c["h"]
+    raw = to_dev(c["raw"], torch.float32)
+    src = to_dev(c["src"], torch.uint8)
+    proj, _ = api.rf_project(raw, c["eps"], c["delta"])
+    Tt = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau, opts=api.make_opts(variant="tiles"))
     st = api.Context.get(0).stats()
-    assert st["status"] == L.RF_ERR_NOT_CONVERGED
-    assert st["sweeps"] < 64 * 64  # stopped early, not at the iteration cap
+    assert st["status"] == 0 and st["converged"], st
+    Tt2 = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau, opts=api.make_opts(variant="tiles"))
+    assert torch.equal(Tt, Tt2)
+    Tj = api.rf_softmin_forward(proj, c["eps"], src, c["h"], tau, opts=api.make_opts(variant="tiled1"))
+    assert api.Context.get(0).stats()["status"] == 0
+    assert (Tt - Tj).abs().max().item() <= FWD_TOL * Tj.max().item()
