@@ -38,8 +38,8 @@ ALG_BYTES_PER_UPDATE = 28  # 5 fields x 4 B + T read 4 B + T write 4 B per node-
 # DRAM bytes (read + write) of one launch of the tile-queue forward kernel on the 2048^2 workload (16x16
 # tiles), by delta-stepping window, each from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # Reported as roofline.traffic only while the kernel's sources hash to the captured build's.
-TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048, 2.0): {"sources_sha16": "e5eece3c1a0a83da", "bytes": 424007168 + 43842304},
-                    ("tile_solve_kernel<16>", 2048, 4.0): {"sources_sha16": "e5eece3c1a0a83da", "bytes": 426858240 + 45993472}}
+TRAFFIC_CAPTURES = {("tile_solve_kernel<16>", 2048, 2.0): {"sources_sha16": "ec162a0fb8fa3692", "bytes": 423551232 + 43747328},
+                    ("tile_solve_kernel<16>", 2048, 4.0): {"sources_sha16": "ec162a0fb8fa3692", "bytes": 427654656 + 46024448}}
 TRAFFIC_SOURCES = ["paper_2603_00035_gb300/csrc/rf_sweep_tiles.cu", "paper_2603_00035_gb300/csrc/rf_cone.cuh",
                    "paper_2603_00035_gb300/csrc/rf_sweep_common.cuh", "paper_2603_00035_gb300/csrc/rf_device.cuh"]
 # kernels of ours per step: project, record, project backward; the forward variant's kernels (init and
