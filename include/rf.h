@@ -418,9 +418,11 @@ rf_status rf_softmin_forward(rf_ctx *ctx, const rf_grid *grid, const float *proj
 rf_status rf_softmin_record(rf_ctx *ctx, const rf_grid *grid, const float *proj5, float eps,
                             const uint8_t *src, const float *T, float tau, float *wnb, float *dT, void *stream);
 /* Adjoint of the relaxed system: lambda_p = g_p + sum over neighbours q of
- * wnb_q(q -> p) lambda_q (iterated until no multiplier changes by more than
- * 1e-7 relative: exact when the weights form a DAG), dLdproj5 = lambda dT
- * (5 planes, zero at sources and unreached nodes); lambda (nullable). */
+ * wnb_q(q -> p) lambda_q, iterated (block Jacobi: 16 x 16 tiles, 16 Jacobi
+ * steps per tile between grid-wide exchanges) until no multiplier changes by
+ * more than 1e-7 relative between two exchanges (their count is the
+ * adj_sweeps statistic), dLdproj5 = lambda dT (5 planes, zero at sources
+ * and unreached nodes); lambda (nullable). */
 rf_status rf_softmin_adjoint(rf_ctx *ctx, const rf_grid *grid, const uint8_t *src, const float *T,
                              const float *wnb, const float *dT, const float *dLdT, float *dLdproj5,
                              float *lambda, void *stream);

@@ -242,35 +242,70 @@ struct SoftAdjArgs {
 };
 
 // lambda_p = g_p + sum over neighbours q of wnb_q(q -> p) lambda_q, iterated
-// (Jacobi) until no multiplier changes by more than 1e-7 relative -- exact
-// after as many iterations as the longest weight path when the weights form
-// a DAG, geometric where a soft value sits below a donor and the weights
-// close a cycle -- then dL/dtheta_p = lambda_p dT_p.
-__global__ void __launch_bounds__(256) softmin_adjoint_kernel(SoftAdjArgs a) {
+// until no multiplier changes by more than 1e-7 relative between two grid
+// barriers, then dL/dtheta_p = lambda_p dT_p.  Block Jacobi: between two
+// grid barriers each 16 x 16 tile runs kSoftInner Jacobi steps in shared
+// memory with its halo held at the previous iterate, so one barrier moves
+// information across a tile instead of one node (the relaxed weights do
+// not form a DAG -- a node also weighs neighbours that are not later than
+// itself -- so the multipliers are a fixed point, not a back-substitution).
+constexpr int kSoftTile = 16;
+constexpr int kSoftInner = 16;
+
+__global__ void __launch_bounds__(kSoftTile * kSoftTile) softmin_adjoint_kernel(SoftAdjArgs a) {
+  constexpr int TS = kSoftTile, HW = TS + 2;
+  __shared__ float lam[2][HW][HW + 1];
   const long long n = (long long)a.ny * a.nx;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = threadIdx.x, li = t / TS, lj = t - (t / TS) * TS;
+  const int tiles_x = (a.nx + TS - 1) / TS, tiles = ((a.ny + TS - 1) / TS) * tiles_x;
   float *cur = a.La, *nxt = a.Lb;
   int it = 0;
   bool converged = false, abort = false;
   for (; it < a.max_iter; ++it) {
     int changed = 0;
-    for (long long p = g0; p < n; p += stride) {
-      float acc = 0.0f;
-      if (a.T[p] < kInf) {
-        const int i = (int)(p / a.nx), j = (int)(p - (long long)i * a.nx);
-        acc = a.g[p];
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-          const int ii = i + nb_dy(nb), jj = j + nb_dx(nb);
-          if (ii < 0 || ii >= a.ny || jj < 0 || jj >= a.nx) continue;
-          const long long q = (long long)ii * a.nx + jj;
-          const float wq = a.wnb[(long long)((nb + 4) & 7) * n + q];
-          if (wq != 0.0f) acc = fmaf(wq, __ldcg(cur + q), acc);
-        }
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const int i0 = (tile / tiles_x) * TS, j0 = (tile % tiles_x) * TS;
+      // the tile and its halo at the previous iterate (0 outside the grid)
+      for (int k = t; k < HW * HW; k += TS * TS) {
+        const int r = k / HW, c = k - (k / HW) * HW, i = i0 + r - 1, j = j0 + c - 1;
+        const float v = (i >= 0 && i < a.ny && j >= 0 && j < a.nx) ? __ldcg(cur + (long long)i * a.nx + j) : 0.0f;
+        lam[0][r][c] = v;
+        lam[1][r][c] = v;
       }
-      changed |= node_changed(acc, __ldcg(cur + p), 0.0f, 1e-7f);
-      __stcg(nxt + p, acc);
+      // this thread's node: g and the weights of its neighbours toward it
+      const int i = i0 + li, j = j0 + lj;
+      const bool in = i < a.ny && j < a.nx;
+      const long long p = in ? (long long)i * a.nx + j : 0;
+      const bool live = in && a.T[p] < kInf;
+      float gp = 0.0f, w[8];
+#pragma unroll
+      for (int nb = 0; nb < 8; ++nb) {
+        w[nb] = 0.0f;
+        const int ii = i + nb_dy(nb), jj = j + nb_dx(nb);
+        if (live && ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx)
+          w[nb] = a.wnb[(long long)((nb + 4) & 7) * n + (long long)ii * a.nx + jj];
+      }
+      if (live) gp = a.g[p];
+      __syncthreads();
+      int b = 0;
+      for (int k = 0; k < kSoftInner; ++k) {
+        float acc = 0.0f;
+        if (live) {
+          acc = gp;
+#pragma unroll
+          for (int nb = 0; nb < 8; ++nb)
+            if (w[nb] != 0.0f) acc = fmaf(w[nb], lam[b][li + 1 + nb_dy(nb)][lj + 1 + nb_dx(nb)], acc);
+        }
+        lam[b ^ 1][li + 1][lj + 1] = acc;
+        b ^= 1;
+        __syncthreads();
+      }
+      if (in) {
+        const float acc = lam[b][li + 1][lj + 1];
+        changed |= node_changed(acc, __ldcg(cur + p), 0.0f, 1e-7f);
+        __stcg(nxt + p, acc);
+      }
+      __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[(it + 1) % 3] = 0;
     if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&a.flags[it % 3], 1);
@@ -278,9 +313,9 @@ __global__ void __launch_bounds__(256) softmin_adjoint_kernel(SoftAdjArgs a) {
       abort = true;
       break;
     }
-    float *t = cur;
+    float *tmp = cur;
     cur = nxt;
-    nxt = t;
+    nxt = tmp;
     if (!ld_acquire_s32(&a.flags[it % 3])) {
       converged = true;
       ++it;
@@ -288,12 +323,13 @@ __global__ void __launch_bounds__(256) softmin_adjoint_kernel(SoftAdjArgs a) {
     }
   }
   if (!abort) {
-    for (long long p = g0; p < n; p += stride) {
-      const float lam = __ldcg(cur + p);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+      const float lp = __ldcg(cur + p);
       const bool act = a.T[p] < kInf && !a.src[p];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) a.grad[c * n + p] = act ? lam * a.dT[c * n + p] : 0.0f;
-      if (a.lam_out) a.lam_out[p] = lam;
+      for (int c = 0; c < 5; ++c) a.grad[c * n + p] = act ? lp * a.dT[c * n + p] : 0.0f;
+      if (a.lam_out) a.lam_out[p] = lp;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -459,9 +495,9 @@ extern "C" rf_status rf_softmin_adjoint(rf_ctx *ctx, const rf_grid *grid, const 
   a.ctl.st = ctx->state;
   a.ctl.abort = ctx->changed + 5;
   a.ctl.timeout_ns = ctx->timeout_ns;
-  const int g = coop_grid(ctx, (const void *)softmin_adjoint_kernel, 256);
+  const int g = coop_grid(ctx, (const void *)softmin_adjoint_kernel, kSoftTile * kSoftTile);
   if (!g) return RF_ERR_UNSUPPORTED;
   void *args[] = {&a};
-  return cuda_status(
-      cudaLaunchCooperativeKernel((const void *)softmin_adjoint_kernel, dim3(g), dim3(256), args, 0, s));
+  return cuda_status(cudaLaunchCooperativeKernel((const void *)softmin_adjoint_kernel, dim3(g),
+                                                 dim3(kSoftTile * kSoftTile), args, 0, s));
 }
