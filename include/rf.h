@@ -487,9 +487,13 @@ rf_status rf_unet_conv3x3(rf_ctx *ctx, const uint16_t *x, int B, int H, int W,
                           void *stream);
 /* The same convolution on the fifth-generation tensor cores (tcgen05.mma,
  * BF16 operands in shared memory, FP32 accumulator in tensor memory): same
- * arguments, same result up to FP32 summation order.  A tensor-core wait
- * that exceeds the context timeout sets RF_ERR_TIMEOUT in the context
- * statistics. */
+ * arguments, same result up to FP32 summation order.  With 64 or more input
+ * channels and Cout a multiple of 64 it first copies w, in the order the
+ * kernel's pipeline stages hold it, into the context's workspace (grown on
+ * first use to Cout * 9 * Cin BF16 values; RF_ERR_NO_MEMORY if that fails),
+ * so two such calls on one context must not run on different streams at
+ * once.  A tensor-core wait that exceeds the context timeout sets
+ * RF_ERR_TIMEOUT in the context statistics. */
 rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, int H,
                              int W, int Cin, const uint16_t *w,
                              const float *bias, int Cout, int relu,

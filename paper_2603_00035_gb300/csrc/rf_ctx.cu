@@ -41,6 +41,7 @@ extern "C" rf_status rf_ctx_destroy(rf_ctx *c) {
   cudaFree(c->tvbuf);
   cudaFree(c->tilebuf);
   cudaFree(c->stepbuf);
+  cudaFree(c->wpack);
   if (c->step_in) cudaStreamDestroy(c->step_in);
   if (c->step_out) cudaStreamDestroy(c->step_out);
   for (cudaEvent_t e : c->step_ev)

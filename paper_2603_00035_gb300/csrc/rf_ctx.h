@@ -37,6 +37,8 @@ struct rf_ctx {
   size_t tvbuf_cap = 0;
   unsigned char *tilebuf = nullptr;  // tile-queue solve: queue, tile states, halos
   size_t tilebuf_cap = 0;
+  uint16_t *wpack = nullptr;  // tcgen05 convolution: BF16 weights in the order its stages hold them
+  size_t wpack_cap = 0;
   unsigned char *stepbuf = nullptr;  // rf_step_host: two input/output sets and the intermediates
   size_t stepbuf_cap = 0;
   cudaStream_t step_in = nullptr, step_out = nullptr;  // rf_step_host: copy streams (created on first use)

@@ -127,6 +127,7 @@ struct TcArgs {
   const bf16 *x;      // [B][H][W][Cin]
   const bf16 *w;      // [Cout][9][Cin]
   const float *bias;  // [Cout] or null
+  bf16 *wpack;        // Cout * 9 * Cin scratch for the packed weights (persistent kernel)
   bf16 *y;            // [B][H][W][Cout]
   float *y32;         // optional FP32 copy
   int B, H, W, Cin, Cout, relu, CC;
@@ -300,7 +301,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
+// One contiguous copy (cp.async.bulk, not tensor-mapped): both addresses
+// 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(m))
+               : "memory");
+}
+
 struct TmaArgs {
+  const bf16 *wpack;  // persistent kernel: the weights in stage order (pack_w_kernel)
   const float *bias;
   bf16 *y;
   float *y32;
@@ -500,9 +511,11 @@ __device__ __forceinline__ TileIdx tile_of(int tile, int tiles_x, int tiles_pix,
 // tiles x N channels; consecutive units share their weights), with two sets
 // of P accumulators in tensor memory so that a unit's epilogue overlaps the
 // next unit's MMAs.
-//  * warp 4 (producer): stage after stage, across units, as in
-//    conv3x3_tma_kernel (16 input channels per stage; the activation box
-//    is 8P + 2 rows high);
+//  * warp 4 (producer): stage after stage, across units, the activation
+//    planes as in conv3x3_tma_kernel (16 input channels per stage; the box
+//    is 8P + 2 rows high), the weight planes by one bulk copy from the
+//    packed weights (pack_w_kernel, launched before on the same stream) or,
+//    without them, by tensor copies of 16-byte rows;
 //  * warp 5, lane 0 (MMA issuer): per unit, waits until the epilogue has
 //    released the unit's accumulator set, issues 9 P MMAs per stage (each
 //    weight stage serves the P tiles), commits each stage to its "empty"
@@ -512,6 +525,28 @@ __device__ __forceinline__ TileIdx tile_of(int tile, int tiles_x, int tiles_pix,
 // Every wait is bounded by the context timeout; a timeout records
 // RF_ERR_TIMEOUT, every role leaves its loop, and the CTA waits (bounded)
 // for the MMAs it issued before freeing TMEM.
+// The weights [Cout][9][Cin] rearranged into the persistent kernel's stage
+// order: block (nt, i) -- output channels nt N .. nt N + N - 1, input
+// channels 16 i .. 16 i + 15 -- is [tap][8-channel half][n][8 channels],
+// byte for byte the B planes a stage holds, so that one bulk copy of
+// stage_b_bytes(N) fills them (the tensor-mapped loads of the same planes
+// move 16-byte rows, 2 * 9 * N of them per stage).  One thread per 16 bytes.
+template <int N>
+__global__ void pack_w_kernel(const bf16 *__restrict__ w, bf16 *__restrict__ wp, int Cin, int Cout) {
+  const int c8n = Cin / 8, nchunks = Cin / 16;
+  const long long total = (long long)Cout * 9 * c8n;
+  const uint4 *src = reinterpret_cast<const uint4 *>(w);
+  uint4 *dst = reinterpret_cast<uint4 *>(wp);
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total;
+       j += (long long)gridDim.x * blockDim.x) {
+    const int c8g = (int)(j % c8n);
+    const long long r = j / c8n;  // co * 9 + tap
+    const int t = (int)(r % 9), co = (int)(r / 9);
+    const int nt = co / N, n = co % N, i = c8g >> 1, c8 = c8g & 1;
+    dst[((((long long)nt * nchunks + i) * 9 + t) * 2 + c8) * N + n] = src[j];
+  }
+}
+
 template <int N, int P>
 __global__ void __launch_bounds__(kPersistThreads, 1)
     conv3x3_persist_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap,
@@ -578,6 +613,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         if (lane < 6) {
           const int kx = lane >> 1, c8 = lane & 1;
           tma_load_4d(sa + (kx * 2 + c8) * PB, &xmap, (c8_0 + c8) * 8, ti.tx0 + kx - 1, ti.ty0 - 1, ti.b, &full[st]);
+        } else if (a.wpack) {
+          if (lane == 6) bulk_load(sb, a.wpack + ((size_t)ti.nt * nchunks + i) * (SB / 2), SB, &full[st]);
         } else if (lane < 24) {
           const int j = lane - 6, t = j >> 1, c8 = j & 1;
           tma_load_3d(sb + (t * 2 + c8) * N * 16, &wmap, (c8_0 + c8) * 8, t, ti.nt * N, &full[st]);
@@ -731,6 +768,7 @@ rf_status encode_maps(const TcArgs &t, CUtensorMap &xmap, CUtensorMap &wmap, int
 
 inline TmaArgs tma_args(const TcArgs &t) {
   TmaArgs a;
+  a.wpack = t.wpack;
   a.bias = t.bias;
   a.y = t.y;
   a.y32 = t.y32;
@@ -776,6 +814,11 @@ rf_status launch_persist(const TcArgs &t, int num_sms, cudaStream_t s) {
       (long long)((t.W + kTW - 1) / kTW) * ((t.H + kTH * P - 1) / (kTH * P)) * (t.Cout / N) * t.B;
   if (ntiles > (1LL << 30)) return RF_ERR_INVALID_ARG;
   const int grid = (int)std::min<long long>(ntiles, num_sms);
+  if (t.wpack) {
+    const long long chunks = (long long)t.Cout * 9 * (t.Cin / 8);
+    pack_w_kernel<N><<<(int)std::min<long long>((chunks + 255) / 256, 4LL * num_sms), 256, 0, s>>>(t.w, t.wpack, t.Cin,
+                                                                                               t.Cout);
+  }
   conv3x3_persist_kernel<N, P><<<grid, kPersistThreads, smem, s>>>(xmap, wmap, a);
   return cuda_status(cudaGetLastError());
 }
@@ -823,6 +866,15 @@ extern "C" rf_status rf_unet_conv3x3_tc(rf_ctx *ctx, const uint16_t *x, int B, i
   a.CC = (Cin % 32 == 0) ? 32 : 16;
   a.st = ctx->state;
   a.timeout_ns = ctx->timeout_ns;
+  // the persistent kernel takes its weight stages from a packed copy when
+  // the layer has 64 or more input and output channels (8 x 128^2 x
+  // 128 -> 128: 447 -> 651 TFLOP/s); narrower layers have too few stages
+  // per unit to repay the packing launch (32 -> 32: 200 -> 115 TFLOP/s)
+  a.wpack = nullptr;
+  if (Cin >= 64 && Cout % 64 == 0) {
+    if (rf_status rw = ensure(&ctx->wpack, &ctx->wpack_cap, (size_t)Cout * 9 * Cin); rw != RF_OK) return rw;
+    a.wpack = reinterpret_cast<tc::bf16 *>(ctx->wpack);
+  }
   // the pipelined tensor-copy kernel; the plain one if a tensor map cannot
   // be encoded here
   rf_status rs = RF_ERR_UNSUPPORTED;

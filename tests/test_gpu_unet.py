@@ -67,13 +67,17 @@ def test_conv3x3_forward_dgrad_wgrad(B, H, W, Cin, Cout, relu):
 @pytest.mark.parametrize("B,H,W,Cin,Cout,relu", [(2, 13, 37, 32, 48, 1), (1, 8, 16, 16, 16, 0), (1, 24, 40, 96, 32, 1),
                                                (1, 16, 32, 64, 64, 1), (2, 9, 20, 128, 64, 0), (1, 8, 16, 384, 128, 1),
                                                (2, 4, 4, 128, 256, 1), (2, 4, 6, 256, 128, 0),
-                                               (8, 32, 256, 16, 32, 1), (4, 64, 192, 16, 128, 0)])
+                                               (8, 32, 256, 16, 32, 1), (4, 64, 192, 16, 128, 0),
+                                               (2, 16, 48, 64, 192, 1), (8, 64, 160, 64, 128, 0)])
 def test_conv3x3_tcgen05_forward_and_dgrad(B, H, W, Cin, Cout, relu):
     """The tcgen05 convolution (BF16 operands in shared memory, FP32
     accumulator in tensor memory) against the FP64 reference, forward and
-    data gradient, and against the mma.sync kernel.  The last two shapes
-    have more than two tiles per SM, so the persistent kernel alternates its
-    two accumulators and waits for the epilogue to release them."""
+    data gradient, and against the mma.sync kernel.  In the larger shapes
+    some CTAs of the persistent kernel take several units, so they
+    alternate their two accumulators and wait for the epilogue to release
+    them (the last one three units).  Layers with 64 or more input and
+    output channels take their weight stages from the packed copy by one
+    bulk copy each, the others by tensor copies."""
     rng = np.random.default_rng(B * 1000 + H * 10 + Cin)
     ctx, lib, s = Context.get(0), L.load(), _stream()
     x_t, x = bf16(rng.standard_normal((B, H, W, Cin)))
